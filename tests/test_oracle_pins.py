@@ -1,0 +1,491 @@
+"""Pins of the FP64 oracle to the paper and to mathematics (no GPU).
+
+Each test checks the oracle against something other than itself: a hand-derived
+closed form of Eq. 1-3, an independent library routine (scipy rotations,
+torch.optim.Adam), a numerical derivative, brute force over tiles, or an
+invariant of the definitions.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from synth import Camera, frustum_scene
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+CFG = O.Config()
+
+
+def _params(means, logscales, quats, logits, rgbs):
+    n = len(means)
+    p = np.zeros((14, n))
+    p[0:3] = np.asarray(means, float).T
+    p[3:6] = np.asarray(logscales, float).reshape(n, 3).T
+    p[6:10] = np.asarray(quats, float).reshape(n, 4).T
+    p[10] = logits
+    p[11:14] = np.asarray(rgbs, float).T
+    return p
+
+
+def _logit(o):
+    return math.log(o / (1.0 - o))
+
+
+def _axis_cam(f=100.0, size=64):
+    return Camera(size, size, f, f, size / 2, size / 2)
+
+
+# ------------------------------------------------------------------ paper constants
+
+
+def test_paper_constants_match_config():
+    g = json.load(open(os.path.join(GOLDEN, "paper_constants.json")))
+    assert CFG.reg_floor == g["reg_floor"]["value"]          # Eq. 10
+    assert CFG.insert_opacity == g["insert_opacity"]["value"]
+    assert CFG.split_thresh == g["split_thresh"]["value"]
+
+
+# ------------------------------------------------------------------ Eq. 1
+
+
+def test_rotation_matches_scipy():
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(3)
+    q = rng.normal(size=(50, 4))
+    R = O.quat_to_rotmat(torch.tensor(q)).numpy()
+    ref = Rotation.from_quat(q[:, [1, 2, 3, 0]]).as_matrix()     # scipy is scalar-last
+    np.testing.assert_allclose(R, ref, atol=1e-13)
+
+
+def test_covariance_of_axis_rotation():
+    # 90 degrees about z maps x->y, y->-x, so Sigma = diag(s2^2, s1^2, s3^2)
+    s = np.array([0.1, 0.2, 0.3])
+    q = np.array([[math.cos(math.pi / 4), 0, 0, math.sin(math.pi / 4)]])
+    S = O.cov3d(torch.tensor(np.log(s))[None], torch.tensor(q)).numpy()[0]
+    np.testing.assert_allclose(S, np.diag([0.04, 0.01, 0.09]), atol=1e-15)
+    # unnormalised quaternion: same rotation
+    S2 = O.cov3d(torch.tensor(np.log(s))[None], torch.tensor(3.7 * q)).numpy()[0]
+    np.testing.assert_allclose(S2, S, atol=1e-15)
+
+
+# ------------------------------------------------------------------ Eq. 2
+
+
+def _pinhole(t, cam):
+    return np.array([cam.fx * t[0] / t[2] + cam.cx, cam.fy * t[1] / t[2] + cam.cy])
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_cov2d_is_numerical_jacobian_sandwich(seed):
+    """Sigma2D - 0.3 I = J W Sigma W^T J^T with J the central-difference Jacobian of the pinhole map."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(seed)
+    Rw = Rotation.from_rotvec(rng.normal(size=3) * 0.5).as_matrix()
+    cam = Camera(320, 240, 300.0, 280.0, 160.0, 120.0, Rw, rng.normal(size=3) * 0.3)
+    # a mean in front of the camera, well inside the FOV clamp
+    tcam = np.array([rng.uniform(-0.5, 0.5), rng.uniform(-0.4, 0.4), rng.uniform(2, 4)])
+    mu = Rw.T @ (tcam - cam.t)
+    ls = rng.normal(-2, 0.4, size=3)
+    q = rng.normal(size=4)
+    p = _params([mu], [ls], [q], [0.0], [[0.5, 0.5, 0.5]])
+    pr = O.project(torch.tensor(p), cam)
+    h = 1e-6
+    J = np.stack([(_pinhole(tcam + h * e, cam) - _pinhole(tcam - h * e, cam)) / (2 * h) for e in np.eye(3)], 1)
+    from scipy.spatial.transform import Rotation as Rt
+    Rg = Rt.from_quat(q[[1, 2, 3, 0]]).as_matrix()
+    Sig = Rg @ np.diag(np.exp(2 * ls)) @ Rg.T
+    expect = J @ Rw @ Sig @ Rw.T @ J.T
+    got = pr["cov2d"].numpy()[0] - CFG.dilation * np.eye(2)
+    np.testing.assert_allclose(got, expect, rtol=1e-7, atol=1e-9)
+    np.testing.assert_allclose([pr["u"].item(), pr["v"].item()], _pinhole(tcam, cam), rtol=1e-12)
+    assert abs(pr["depth"].item() - tcam[2]) < 1e-12
+    # conic is the inverse of the dilated covariance
+    cov = pr["cov2d"].numpy()[0]
+    inv = np.linalg.inv(cov)
+    np.testing.assert_allclose([pr["a"].item(), pr["b"].item(), pr["c"].item()], [inv[0, 0], inv[0, 1], inv[1, 1]],
+                               rtol=1e-10)
+
+
+def test_isotropic_on_axis_closed_form():
+    """Identity pose, mean (0, 0, z), isotropic scale s: Sigma2D = ((f s / z)^2 + 0.3) I."""
+    f, z, s, o = 100.0, 2.0, 0.05, 0.5
+    cam = _axis_cam(f)
+    c = [0.2, 0.6, 1.0]
+    p = _params([[0, 0, z]], [[math.log(s)] * 3], [[1, 0, 0, 0]], [_logit(o)], [c])
+    pr = O.project(torch.tensor(p), cam)
+    sig2 = (f * s / z) ** 2 + 0.3                               # 6.55
+    np.testing.assert_allclose(pr["cov2d"].numpy()[0], sig2 * np.eye(2), rtol=1e-14)
+    lam = sig2 + math.sqrt(0.1)                                  # discriminant 0 floored at 0.1
+    r = math.ceil(3 * math.sqrt(lam))
+    assert r == 8 and pr["r"].item() == r
+    offsets = [(0, 0), (3, 0), (0, -4), (5, 5), (7, 0), (8, 0), (9, 0), (-6, 3), (8, 8), (-8, 7)]
+    pix = np.array([[32 + dx, 32 + dy] for dx, dy in offsets])
+    out = O.render(p, cam, pixels=pix)
+    for k, (dx, dy) in enumerate(offsets):
+        a = min(0.99, o * math.exp(-(dx * dx + dy * dy) / (2 * sig2)))
+        if max(abs(dx), abs(dy)) > r or a < 1 / 255:
+            a = 0.0
+        np.testing.assert_allclose(out["rgb"][k], np.array(c) * a, rtol=1e-12, atol=1e-300)
+        np.testing.assert_allclose(out["T"][k], 1 - a, rtol=1e-12)
+    # (8, 0): alpha = 0.5 exp(-64/13.1) = 0.00378 < 1/255 is skipped although a member;
+    # (7, 0): 0.0119 blends
+    assert out["n_contrib"][offsets.index((8, 0))] == 0
+    assert out["n_contrib"][offsets.index((7, 0))] == 1
+
+
+def test_off_axis_isotropic_hand_jacobian():
+    """Off-axis isotropic Gaussian: J = [[f/z, 0, -f x/z^2], [0, f/z, -f y/z^2]] written by hand."""
+    f, s = 120.0, 0.07
+    x, y, z = 0.3, -0.2, 2.5
+    cam = _axis_cam(f, 96)
+    p = _params([[x, y, z]], [[math.log(s)] * 3], [[0.3, 0.1, -0.5, 0.2]], [0.0], [[1, 1, 1]])
+    pr = O.project(torch.tensor(p), cam)
+    J = np.array([[f / z, 0, -f * x / z ** 2], [0, f / z, -f * y / z ** 2]])
+    expect = s * s * J @ J.T + 0.3 * np.eye(2)                   # rotation-invariant (isotropic)
+    np.testing.assert_allclose(pr["cov2d"].numpy()[0], expect, rtol=1e-13)
+
+
+def test_fov_clamp_of_jacobian():
+    """Beyond 1.3 x the half-FOV tangent, J uses the clamped x/z (reading of Eq. 2)."""
+    f, s, z = 100.0, 0.05, 1.0
+    cam = _axis_cam(f, 64)                       # half-FOV tangent 0.32 -> clamp 0.416
+    x = 0.8                                      # x/z = 0.8 > 0.416
+    p = _params([[x, 0, z]], [[math.log(s)] * 3], [[1, 0, 0, 0]], [0.0], [[1, 1, 1]])
+    pr = O.project(torch.tensor(p), cam)
+    xh = 1.3 * 0.32
+    J = np.array([[f / z, 0, -f * xh / z], [0, f / z, 0]])
+    np.testing.assert_allclose(pr["cov2d"].numpy()[0], s * s * J @ J.T + 0.3 * np.eye(2), rtol=1e-13)
+    assert bool(pr["tclamp"][0, 0]) and not bool(pr["tclamp"][0, 1])
+
+
+def test_culling_near_plane_and_offscreen():
+    cam = _axis_cam()
+    p = _params([[0, 0, 0.19], [0, 0, 0.21], [100, 0, 1.0], [0, 0, -1.0]], [[-3] * 3] * 4,
+                [[1, 0, 0, 0]] * 4, [0.0] * 4, [[1, 1, 1]] * 4)
+    pr = O.project(torch.tensor(p), cam)
+    assert pr["valid"].tolist() == [False, True, False, False]
+
+
+# ------------------------------------------------------------------ Eq. 3
+
+
+def _stack(opacities, rgbs, depths, scale=0.3):
+    n = len(depths)
+    return _params([[0, 0, d] for d in depths], [[math.log(scale)] * 3] * n, [[1, 0, 0, 0]] * n,
+                   [_logit(o) for o in opacities], rgbs)
+
+
+def test_stack_alpha_095_closed_form():
+    """Five layers with alpha 0.95 at their common centre pixel: T after k layers is 0.05^k;
+    0.05^4 = 6.25e-6 < 1e-4 stops before the fourth, so three layers blend."""
+    cols = [[0.9, 0.1, 0.2], [0.3, 0.8, 0.1], [0.2, 0.3, 0.7], [0.5, 0.5, 0.5], [1.0, 1.0, 0.0]]
+    p = _stack([0.95] * 5, cols, [1, 2, 3, 4, 5])
+    out = O.render(p, _axis_cam(), pixels=np.array([[32, 32]]))
+    expect = sum(np.array(cols[i]) * 0.95 * 0.05 ** i for i in range(3))
+    np.testing.assert_allclose(out["rgb"][0], expect, rtol=1e-13)
+    np.testing.assert_allclose(out["T"][0], 0.05 ** 3, rtol=1e-12)
+    assert out["n_contrib"][0] == 3 and out["last"][0] == 2 and out["argmax"][0] == 0
+
+
+def test_stack_alpha_099_boundary():
+    """o = 0.999 is clamped to alpha = 0.99. In float64 T after two layers is 1.0000000000000018e-4,
+    not below 1e-4, so two layers blend (the float32 case falls below and blends one)."""
+    cols = [[0.9, 0.1, 0.2], [0.3, 0.8, 0.1], [0.2, 0.3, 0.7]]
+    p = _stack([0.999] * 3, cols, [1, 2, 3])
+    out = O.render(p, _axis_cam(), pixels=np.array([[32, 32]]))
+    t1 = 1 - 0.99
+    np.testing.assert_allclose(out["rgb"][0], 0.99 * np.array(cols[0]) + 0.99 * t1 * np.array(cols[1]), rtol=1e-13)
+    assert out["n_contrib"][0] == 2
+    np.testing.assert_allclose(out["T"][0], t1 * t1, rtol=1e-12)
+
+
+def test_transmittance_is_product():
+    rng = np.random.default_rng(5)
+    ops = rng.uniform(0.05, 0.5, size=6)
+    cols = rng.uniform(size=(6, 3))
+    p = _stack(ops, cols, [1, 1.5, 2, 2.5, 3, 3.5])
+    out = O.render(p, _axis_cam(), pixels=np.array([[32, 32]]))
+    np.testing.assert_allclose(out["T"][0], np.prod(1 - ops), rtol=1e-12)
+    expect = sum(cols[i] * ops[i] * np.prod(1 - ops[:i]) for i in range(6))
+    np.testing.assert_allclose(out["rgb"][0], expect, rtol=1e-12)
+
+
+def test_alpha_min_is_strict_threshold():
+    c = [0.5, 0.25, 1.0]
+    for o, blends in [(1 / 255 + 1e-6, True), (1 / 255 - 1e-6, False)]:
+        p = _stack([o], [c], [2.0])
+        out = O.render(p, _axis_cam(), pixels=np.array([[32, 32]]))
+        if blends:
+            np.testing.assert_allclose(out["rgb"][0], np.array(c) * o, rtol=1e-12)
+        else:
+            assert np.all(out["rgb"][0] == 0) and out["T"][0] == 1.0
+
+
+def test_depth_order_and_array_order_invariance():
+    """Front red (depth 1), back blue (depth 2), o = 0.6: C = 0.6 red + 0.24 blue whatever the array order."""
+    red, blue = [1, 0, 0], [0, 0, 1]
+    for depths, cols in [([1, 2], [red, blue]), ([2, 1], [blue, red])]:
+        p = _stack([0.6, 0.6], cols, depths)
+        out = O.render(p, _axis_cam(), pixels=np.array([[32, 32]]))
+        np.testing.assert_allclose(out["rgb"][0], [0.6, 0.0, 0.24], rtol=1e-13, atol=1e-16)
+        np.testing.assert_allclose(out["T"][0], 0.16, rtol=1e-13)
+
+
+def test_full_image_permutation_invariance():
+    p, cam = frustum_scene(n=200, width=48, height=40, fx=60, fy=60, cx=24, cy=20, seed=7)
+    perm = np.random.default_rng(1).permutation(200)
+    a = O.render(p, cam)
+    b = O.render(p[:, perm], cam)
+    # identical blending order; batched BLAS calls may round the last bit differently by position
+    np.testing.assert_allclose(a["rgb"], b["rgb"], rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(a["T"], b["T"], rtol=1e-14)
+    np.testing.assert_array_equal(perm[b["last"][b["last"] >= 0]], a["last"][a["last"] >= 0])
+
+
+def test_pixel_membership_box():
+    """A Gaussian is seen only inside |px-u| <= r, |py-v| <= r; opaque and huge inside."""
+    cam = _axis_cam(100.0, 64)
+    p = _params([[0.005, -0.003, 1.0]], [[math.log(0.03)] * 3], [[1, 0, 0, 0]], [_logit(0.9)], [[1, 1, 1]])
+    pr = O.project(torch.tensor(p), cam)
+    u, v, r = pr["u"].item(), pr["v"].item(), pr["r"].item()
+    out = O.render(p, cam)
+    ys, xs = np.nonzero(out["n_contrib"] > 0)
+    assert np.all(np.abs(xs - u) <= r) and np.all(np.abs(ys - v) <= r)
+
+
+# ------------------------------------------------------------------ binning and sort
+
+
+def _brute_pairs(u, v, r, depth, valid, W, H, tile):
+    ntx, nty = -(-W // tile), -(-H // tile)
+    out = []
+    for ty in range(nty):
+        for tx in range(ntx):
+            for i in range(len(u)):
+                if not valid[i]:
+                    continue
+                # pixels of this tile that pass the membership box
+                hit = False
+                for py in range(ty * tile, min(H, (ty + 1) * tile)):
+                    if abs(py - v[i]) > r[i]:
+                        continue
+                    for px in range(tx * tile, min(W, (tx + 1) * tile)):
+                        if abs(px - u[i]) <= r[i]:
+                            hit = True
+                            break
+                    if hit:
+                        break
+                if hit:
+                    key = ((ty * ntx + tx) << 32) | int(np.float32(depth[i]).view(np.uint32))
+                    out.append((key, i))
+    out.sort()
+    return out
+
+
+@pytest.mark.parametrize("tile", [4, 8, 16])
+def test_bin_pairs_brute_force(tile):
+    p, cam = frustum_scene(n=40, width=37, height=29, fx=40, fy=40, cx=18.5, cy=14.5, seed=11)
+    pr = O.project(torch.tensor(p, dtype=torch.float64), cam)
+    u = pr["u"].numpy().astype(np.float32).astype(np.float64)
+    v = pr["v"].numpy().astype(np.float32).astype(np.float64)
+    r, d, ok = pr["r"].numpy(), pr["depth"].numpy().astype(np.float32), pr["valid"].numpy()
+    keys, vals = O.bin_pairs(u, v, r, d, ok, cam.width, cam.height, tile)
+    ref = _brute_pairs(u, v, r, d, ok, cam.width, cam.height, tile)
+    assert [(int(k), int(x)) for k, x in zip(keys, vals)] == ref
+    cnt = O.tiles_touched(u, v, r, ok, cam.width, cam.height, tile)
+    assert cnt.sum() == len(ref)
+
+
+# ------------------------------------------------------------------ Eq. 10-11 and gradients
+
+
+def test_l1_gradient_of_colour_closed_form():
+    """dL/dc of a lone Gaussian = lambda/(3HW) sum_p sign(C_p - I_p) alpha_p (its blend weight)."""
+    cam = _axis_cam(100.0, 24)
+    p = _params([[0.01, 0.02, 1.0]], [[math.log(0.04)] * 3], [[1, 0.2, 0, 0]], [0.3], [[0.3, 0.6, 0.9]])
+    tg = np.random.default_rng(0).uniform(size=(1, 3, 24, 24))
+    res = O.loss_and_grads(p, [cam], tg)
+    img = res["images"][0]
+    alpha = 1 - res["T"][0]                       # single Gaussian: weight = alpha = 1 - T
+    expect = (np.sign(img - tg[0]) * alpha[None]).sum((1, 2)) / (3 * 24 * 24)
+    np.testing.assert_allclose(res["grad"][11:14, 0], expect, rtol=1e-12)
+
+
+def test_planar_gradient_closed_form():
+    """With nothing in view, dL/dlog-scale = (lambda_reg / N) s_min on the smallest axis if s_min > 0.01."""
+    cam = _axis_cam()
+    ls = [[math.log(0.05), math.log(0.02), math.log(0.3)], [math.log(0.005), 0.0, 0.0], [-1.0, -2.0, -1.5]]
+    p = _params([[0, 0, -1]] * 3, ls, [[1, 0, 0, 0]] * 3, [0.0] * 3, [[1, 1, 1]] * 3)
+    res = O.loss_and_grads(p, [cam], np.zeros((1, 3, 64, 64)))
+    g = res["grad"][3:6]
+    expect = np.zeros((3, 3))
+    expect[1, 0] = 0.02 / 3                       # min 0.02 on axis 1
+    expect[1, 2] = math.exp(-2.0) / 3             # min exp(-2) on axis 1
+    np.testing.assert_allclose(g, expect, rtol=1e-12, atol=1e-300)
+    assert res["reg"] == pytest.approx((0.02 + 0.01 + math.exp(-2.0)) / 3, rel=1e-13)
+    assert np.all(res["grad"][[0, 1, 2, 6, 7, 8, 9, 10, 11, 12, 13]] == 0)
+
+
+def _fd_check(p, cams, tg, rows=None, cols=None, rel_h=1e-5, tol=1e-5):
+    """Central differences with h = rel_h max(1, |p|). Bound: tol |g| plus the float64
+    rounding of the difference quotient, 100 eps |L| / h."""
+    res = O.loss_and_grads(p, cams, tg)
+    g = res["grad"]
+    L = abs(res["loss"])
+    base = O.decision_signature(p, cams)
+    rows = range(14) if rows is None else rows
+    cols = range(p.shape[1]) if cols is None else cols
+    checked = skipped = 0
+    worst = 0.0
+    scale = np.abs(g).max()
+    for i in rows:
+        for j in cols:
+            h = rel_h * max(1.0, abs(p[i, j]))
+            pp, pm = p.copy(), p.copy()
+            pp[i, j] += h
+            pm[i, j] -= h
+            if O.decision_signature(pp, cams) != base or O.decision_signature(pm, cams) != base:
+                skipped += 1
+                continue
+            fd = (O.loss_value(pp, cams, tg) - O.loss_value(pm, cams, tg)) / (2 * h)
+            bound = tol * abs(g[i, j]) + 100 * np.finfo(float).eps * L / h
+            assert abs(fd - g[i, j]) <= bound, (i, j, fd, g[i, j], bound)
+            worst = max(worst, abs(fd - g[i, j]) / max(abs(g[i, j]), 1e-3 * scale))
+            checked += 1
+    return checked, skipped
+
+
+@pytest.mark.parametrize("seed,n", [(0, 1), (1, 3), (2, 5)])
+def test_gradient_finite_differences_tiny(seed, n):
+    """Central differences of the Eq. 11 loss vs the oracle's gradient on 16x16 scenes, random pose."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(100 + seed)
+    Rw = Rotation.from_rotvec(rng.normal(size=3) * 0.2).as_matrix()
+    cam = Camera(16, 16, 20.0, 22.0, 8.0, 7.5, Rw, rng.normal(size=3) * 0.05)
+    tc = np.stack([rng.uniform(-0.25, 0.25, n), rng.uniform(-0.25, 0.25, n), rng.uniform(1.0, 2.0, n)], 1)
+    mu = (tc - cam.t) @ Rw
+    p = _params(mu, rng.normal(-2.0, 0.3, size=(n, 3)), rng.normal(size=(n, 4)), rng.normal(0.5, 1, n),
+                rng.uniform(size=(n, 3)))
+    tg = rng.uniform(size=(1, 3, 16, 16))
+    checked, skipped = _fd_check(p, [cam], tg)
+    assert checked >= 0.8 * 14 * n
+
+
+@pytest.mark.slow
+def test_gradient_finite_differences_64_gaussians_32px():
+    """The 64-Gaussian 32x32 subset of the stream workload, two views (window loss)."""
+    p, cam = frustum_scene(n=64, width=32, height=32, fx=30, fy=30, cx=16, cy=16, seed=21)
+    from scipy.spatial.transform import Rotation
+    cam2 = Camera(32, 32, 30.0, 30.0, 16.0, 16.0, Rotation.from_rotvec([0.05, -0.08, 0.02]).as_matrix(),
+                  np.array([0.05, 0.0, 0.1]))
+    tg = np.random.default_rng(2).uniform(size=(2, 3, 32, 32))
+    p = p.astype(np.float64)
+    cols = np.random.default_rng(3).choice(64, size=16, replace=False)
+    checked, skipped = _fd_check(p, [cam, cam2], tg, cols=cols)
+    assert checked >= 0.8 * 14 * 16
+
+
+def test_window_gradient_is_sum_of_views():
+    p, cam = frustum_scene(n=60, width=32, height=24, fx=30, fy=30, cx=16, cy=12, seed=4)
+    from scipy.spatial.transform import Rotation
+    cam2 = Camera(32, 24, 30.0, 30.0, 16.0, 12.0, Rotation.from_rotvec([0.02, 0.1, 0.0]).as_matrix(),
+                  np.array([0.1, 0.0, 0.0]))
+    tg = np.random.default_rng(0).uniform(size=(2, 3, 24, 32))
+    cfg0 = O.Config(lambda_reg=0.0)
+    both = O.loss_and_grads(p, [cam, cam2], tg, cfg0)
+    a = O.loss_and_grads(p, [cam], tg[:1], cfg0)
+    b = O.loss_and_grads(p, [cam2], tg[1:], cfg0)
+    np.testing.assert_allclose(both["grad"], a["grad"] + b["grad"], rtol=1e-12, atol=1e-18)
+
+
+# ------------------------------------------------------------------ Adam
+
+
+def test_adam_matches_torch_optim():
+    rng = np.random.default_rng(9)
+    p0 = rng.normal(size=(14, 7))
+    cfg = O.Config()
+    tp = [torch.nn.Parameter(torch.tensor(p0[i:i + 1].copy())) for i in range(14)]
+    opt = torch.optim.Adam([{"params": [tp[i]], "lr": cfg.lr[O.PARAM_GROUP_OF_ROW[i]]} for i in range(14)],
+                           betas=(cfg.beta1, cfg.beta2), eps=cfg.eps)
+    p, m, v = p0.copy(), np.zeros_like(p0), np.zeros_like(p0)
+    for step in range(1, 6):
+        g = rng.normal(size=p0.shape) * 10 ** rng.uniform(-6, 0)
+        for i in range(14):
+            tp[i].grad = torch.tensor(g[i:i + 1].copy())
+        opt.step()
+        p, m, v = O.adam_step(p, g, m, v, step, cfg)
+        np.testing.assert_allclose(p, np.concatenate([t.detach().numpy() for t in tp]), rtol=1e-12, atol=1e-15)
+
+
+def test_adam_first_step_closed_form():
+    g = np.array([[1e-3, -2.0, 0.0]] * 14)
+    p1, _, _ = O.adam_step(np.zeros((14, 3)), g, np.zeros((14, 3)), np.zeros((14, 3)), 1)
+    lr = np.array([CFG.lr[O.PARAM_GROUP_OF_ROW[i]] for i in range(14)])[:, None]
+    np.testing.assert_allclose(p1, -lr * g / (np.abs(g) + CFG.eps), rtol=1e-12)
+
+
+# ------------------------------------------------------------------ insertion, initialisation, split
+
+
+def test_insertion_empty_map_and_opaque_wall():
+    cam = _axis_cam(100.0, 64)
+    pts = np.array([[0.0, 0.0, 2.0], [0.1, -0.1, 3.0], [5.0, 0.0, 1.0], [0, 0, -1.0]])
+    mask, pix, inside = O.insertion_mask(pts, cam, np.ones((64, 64)))
+    assert mask.tolist() == [True, True, True, True]
+    assert inside.tolist() == [True, True, False, False]
+    T = np.ones((64, 64))
+    T[32, 32] = 0.005          # opacity 0.995 > 0.99 at the first point's pixel
+    T[29, 35] = 0.02           # opacity 0.98 at the second point's pixel (35.33, 28.67): still inserted
+    mask, pix, _ = O.insertion_mask(pts, cam, T)
+    assert pix[1].tolist() == [35, 29]
+    assert mask.tolist() == [False, True, True, True]
+
+
+def test_plain_init_knn_scale():
+    E = np.array([[0, 0, 0], [0.03, 0, 0], [0, 0.04, 0], [5, 5, 5.0]])
+    X = np.array([[0.0, 0.0, 0.0], [10.0, 10.0, 10.0]])
+    img = np.zeros((3, 4, 4))
+    img[:, 1, 2] = [0.1, 0.2, 0.3]
+    out = O.plain_init(X, np.array([[2, 1], [0, 0]]), img, E)
+    np.testing.assert_allclose(out[3:6, 0], math.log(math.sqrt((0 + 0.03 ** 2 + 0.04 ** 2) / 3)), rtol=1e-12)
+    assert out[3, 1] == -1.0                      # far away: clamped at -1
+    np.testing.assert_allclose(out[11:14, 0], [0.1, 0.2, 0.3])
+    assert out[6, 0] == 1 and out[10, 0] == 0
+
+
+def test_split_children_distribution_and_conservation():
+    n = 100_000
+    rng = np.random.default_rng(0)
+    q = np.array([0.8, 0.2, -0.3, 0.1])
+    ls = np.log([0.02, 0.05, 0.1])
+    P = _params([[1.0, 2.0, 3.0]] * n, [ls] * n, [q] * n, [0.4] * n, [[0.1, 0.2, 0.3]] * n)
+    z = rng.normal(size=(n, 2, 3))
+    newP, newm, newv, mask = O.split(P, np.ones_like(P), np.ones_like(P), np.full(n, 1.0), np.full(n, 1000.0), z)
+    assert mask.all() and newP.shape[1] == 2 * n
+    mu = newP[0:3].T
+    np.testing.assert_allclose(mu.mean(0), [1, 2, 3], atol=4 * 0.1 / math.sqrt(2 * n))
+    from scipy.spatial.transform import Rotation
+    R = Rotation.from_quat(q[[1, 2, 3, 0]]).as_matrix()
+    Sig = R @ np.diag(np.exp(2 * ls)) @ R.T
+    np.testing.assert_allclose(np.cov(mu.T), Sig, atol=5e-4 * 0.01 + 2e-4 * np.abs(Sig).max())
+    np.testing.assert_allclose(newP[3:6], (ls - math.log(1.6))[:, None] * np.ones((1, 2 * n)), rtol=1e-14)
+    assert np.all(newP[6:10] == q[:, None]) and np.all(newP[10] == 0.4)
+    assert np.all(newP[11:14] == np.array([[0.1], [0.2], [0.3]]))
+    assert np.all(newm == 0) and np.all(newv == 0)
+
+
+def test_split_threshold_and_order():
+    P = np.arange(14 * 4, dtype=float).reshape(14, 4)
+    P[6:10] = [[1], [0], [0], [0]]
+    gsum = np.array([1e-3, 1e-5, 3e-4, 0.0])
+    gcnt = np.array([2, 1, 1, 0])             # means 5e-4, 1e-5, 3e-4, never visible
+    z = np.zeros((4, 2, 3))
+    newP, _, _, mask = O.split(P, P, P, gsum, gcnt, z)
+    assert mask.tolist() == [True, False, True, False]
+    np.testing.assert_array_equal(newP[0:3, :2], P[0:3, [1, 3]])      # survivors first, in order
+    np.testing.assert_array_equal(newP[0:3, 2:], P[0:3, [0, 0, 2, 2]])  # then children, z = 0
