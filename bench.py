@@ -1,0 +1,347 @@
+"""Benchmark of the mapping iteration (render -> L1 + planar loss -> adjoint -> Adam).
+
+Workload (default): one Replica-shaped keyframe, 300,000 Gaussians sampled on a
+synthetic textured room (6 planes + 20 boxes), 1200x680, fx = fy = 600, target
+= the room's analytic ray-cast. Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (host cores). Under torchrun every rank runs its own replica of the
+workload (independent keyframes: weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "mapping fwd+bwd iters/s @1200x680,300k Gaussians; time-to-PSNR vs plain"
+UNIT = "iters/s"
+WORKLOAD = ("replica-shaped single keyframe: 300k Gaussians on a textured room (6 planes + 20 boxes), "
+            "1200x680, fx=fy=600; one iteration = render + L1/planar loss + adjoint + Adam")
+N_GAUSS, W, H = 300_000, 1200, 680
+L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2
+
+# Algorithmic FP32 operations per (pixel, Gaussian) pair, counted from the
+# compositing arithmetic (an FMA counts 2): a tested pair costs the offset, the
+# exponent and alpha; a blended pair adds the transmittance update and the
+# weighted colour; the adjoint adds the colour, alpha and conic/mean gradients.
+FLOP_FWD_TESTED, FLOP_FWD_BLENDED = 12, 10
+FLOP_BWD_WALKED, FLOP_BWD_BLENDED = 12, 50
+FP32_LANES_PER_SM = 128
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def make_workload(seed: int = 0):
+    from synth import make_room, room_camera_single, room_gaussians
+    room = make_room(seed)
+    cam = room_camera_single(W, H, 600.0, 600.0)
+    params = room_gaussians(room, N_GAUSS, seed)
+    cache = os.path.join(tempfile.gettempdir(), f"gs_room_target_{seed}_{W}x{H}.npy")
+    if os.path.exists(cache):
+        target = np.load(cache)
+    else:
+        target = room.raycast(cam)
+        try:
+            np.save(cache, target)
+        except OSError:
+            pass
+    return params, cam, target
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = []
+        for ln in open(self.f.name).read().splitlines():
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- CPU oracle
+
+
+def oracle_sample(params, cam, target, n_tiles: int, seed: int):
+    """Oracle fwd+bwd+Adam on ``n_tiles`` random 16x16 pixel tiles of the workload.
+
+    Returns (seconds, fraction of the full image's pixels covered).
+    """
+    import torch
+    import oracle as O
+    rng = np.random.default_rng(seed)
+    pix = []
+    for _ in range(n_tiles):
+        x0 = int(rng.integers(0, W - 16))
+        y0 = int(rng.integers(0, H - 16))
+        yy, xx = np.mgrid[y0:y0 + 16, x0:x0 + 16]
+        pix.append(np.stack([xx.ravel(), yy.ravel()], 1))
+    pix = np.concatenate(pix)
+    p64 = params.astype(np.float64)
+    t0 = time.perf_counter()
+    res = O.loss_and_grads(p64, [cam], target[None], pixels=[pix], chunk=256)
+    O.adam_step(p64, res["grad"], np.zeros_like(p64), np.zeros_like(p64), 1)
+    dt = time.perf_counter() - t0
+    return dt, pix.shape[0] / float(W * H), torch.get_num_threads()
+
+
+def run_reference(args):
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return 0
+    params, cam, target = make_workload(0)
+    tiles_per_step = 4
+    for w in range(args.warmup):
+        oracle_sample(params, cam, target, 1, 1000 + w)
+    secs, frac = 0.0, 0.0
+    cores = 1
+    for k in range(args.steps):
+        dt, f, cores = oracle_sample(params, cam, target, tiles_per_step, k)
+        secs += dt
+        frac += f
+    value = frac / secs                    # full iterations per second
+    sample = (f"{args.steps} steps x {tiles_per_step} random 16x16 tiles ({tiles_per_step * 256} of {W * H} pixels) "
+              f"of the full workload: FP64 fwd+bwd over all 300k Gaussians + Adam, scaled by pixel fraction")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": W, "height": H},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU path
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    from paper_2504_02437_gb300 import build as B
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    barrier(world)
+    from paper_2504_02437_gb300.api import GaussianMap
+
+    params, cam, target = make_workload(seed=rank)
+    dev = torch.device("cuda", local)
+    gm = GaussianMap(capacity=N_GAUSS, max_views=1, max_width=W, max_height=H, device=local,
+                     tile_size=args.tile)
+    p0 = torch.as_tensor(params, device=dev)
+    gm.set_params(p0)
+    tgt = torch.as_tensor(target[None], device=dev).contiguous()
+    loss = torch.empty(3, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        gm.iterate(cam, tgt, loss)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region (L2 flushed between iterations)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    gm.timing(True)
+    launches0 = gm.launches
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            gm.iterate(cam, tgt, loss)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    launches = gm.launches - launches0
+    phases = gm.timing_read()
+    gm.timing(False)
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    total_ms = max_over_ranks(total_ms, world)
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1000.0)
+    final_loss = loss.cpu().numpy().tolist()
+
+    # ---- end to end through the API: target H2D from pinned host, loss D2H, every step
+    tgt_host = torch.as_tensor(target[None]).pin_memory()
+    loss_host = torch.empty(3).pin_memory()
+    e_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        e_s[k].record(stream)
+        tgt.copy_(tgt_host, non_blocking=True)
+        gm.iterate(cam, tgt, loss)
+        loss_host.copy_(loss, non_blocking=True)
+        e_e[k].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(e_s, e_e)), world)
+    e2e_value = world * args.steps / (e2e_ms / 1000.0)
+
+    # ---- roofline of the dominant kernel
+    work = gm.debug_work()
+    per = {k: v[0] / max(v[1], 1) for k, v in phases.items()}
+    dom = max(per, key=per.get)
+    peaks, peak_src = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    if dom == "raster_bwd":
+        flops = FLOP_BWD_WALKED * work["walked"] + FLOP_BWD_BLENDED * work["blended"]
+        roof = {"bound": "alu", "achieved": flops / (per[dom] * 1e-3) / 1e12, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s"}
+    elif dom == "raster_fwd":
+        flops = FLOP_FWD_TESTED * work["tested"] + FLOP_FWD_BLENDED * work["blended"]
+        roof = {"bound": "alu", "achieved": flops / (per[dom] * 1e-3) / 1e12, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s"}
+    else:
+        # memory-bound phases: algorithmic bytes per unit (see the design notes' table)
+        P, N = work["pairs"], gm.n
+        bytes_model = {"project": 56 * N + 64 * N + 4 * 8 * 2 * N, "bin": 2 * 16 * P + 8 * P,
+                       "loss": 3 * 4 * 3 * W * H, "project_bwd": 56 * N + 48 * N + 56 * N,
+                       "adam": 14 * N * 4 * 7}
+        roof = {"bound": "hbm", "achieved": bytes_model[dom] / (per[dom] * 1e-3) / 1e9,
+                "peak": float(peaks["hbm_gbs"]), "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = dom
+    roof["peak_source"] = ("FP32 lanes x 2 x SMs x max SM clock" if roof["bound"] == "alu"
+                           else f"MEASURED_PEAKS.json hbm_gbs ({peak_src})")
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": W, "height": H,
+                       "tile": gm.tile_size, "l2": "flushed between iterations (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(tgt.numel() * 4),
+                    "d2h_bytes_per_step": 12},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "clocks": clk.summary(),
+            "phases_ms": {k: round(v, 5) for k, v in per.items()},
+            "work": work, "final_loss": final_loss}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        dt, frac, cores = oracle_sample(params, cam, target, args.cpu_tiles, 7)
+        line["cpu_baseline"] = {"value": frac / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{args.cpu_tiles} random 16x16 tiles ({args.cpu_tiles * 256} of {W * H} "
+                                          f"pixels): FP64 fwd+bwd over all 300k Gaussians + Adam, "
+                                          f"{dt:.1f} s, scaled by pixel fraction"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    gm.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile", type=int, default=16, choices=[0, 8, 16])
+    ap.add_argument("--cpu-tiles", type=int, default=16)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

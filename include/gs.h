@@ -1,0 +1,234 @@
+/*
+ * gs.h - C ABI of the GB300 (sm_103a) mapping hot path of MonoGS++
+ * (arXiv 2504.02437): differentiable 3D Gaussian splatting forward and
+ * backward passes, the photometric + planar loss, Adam, dynamic insertion
+ * and densification, over a window of keyframes.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Gaussian parameters are float32, planar SoA of shape [14][n]:
+ *   rows 0-2 mean xyz (mu, Eq. 1), 3-5 log-scale (s = exp(.), Eq. 1),
+ *   6-9 quaternion w,x,y,z (r of Eq. 1; normalised inside the forward pass),
+ *   10 opacity logit (alpha = sigmoid(.)), 11-13 RGB colour (c of Eq. 1, k = 3).
+ * - Images are float32, contiguous, channel-planar [n_views][3][H][W];
+ *   per-pixel maps are [n_views][H][W].
+ * - Pointers named *_dev are device pointers on the context's device; the
+ *   library never frees caller memory. Pointers named *_host are host memory.
+ * - `stream` is a cudaStream_t (NULL = legacy default stream). Every call
+ *   enqueues its work on that stream and returns without waiting, unless its
+ *   comment says it synchronises.
+ * - Return value: GS_OK (0) or a negative GS_ERR_* code; gs_last_error()
+ *   then holds a message. A call that fails with GS_ERR_ARG or
+ *   GS_ERR_CAPACITY leaves the map state (parameters, Adam moments,
+ *   densification statistics) unchanged.
+ * - A context is bound to one device and is not thread-safe; use one context
+ *   per host thread and keep its calls on one stream.
+ */
+#ifndef GS_GB300_H
+#define GS_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GS_API __attribute__((visibility("default")))
+#else
+#define GS_API
+#endif
+
+#define GS_OK 0
+#define GS_ERR_ARG (-1)        /* invalid argument (null pointer, size, camera)          */
+#define GS_ERR_OOM (-2)        /* device or pinned-host allocation failed               */
+#define GS_ERR_CAPACITY (-3)   /* more Gaussians or pairs than the context can hold     */
+#define GS_ERR_CUDA (-4)       /* a CUDA runtime call or kernel launch failed           */
+#define GS_ERR_TIMEOUT (-5)    /* a bounded device-side wait gave up                    */
+#define GS_ERR_NONFINITE (-6)  /* a non-finite loss or parameter was detected          */
+#define GS_ERR_STATE (-7)      /* call out of order (e.g. backward before render)       */
+
+#define GS_MAX_VIEWS 16
+
+typedef struct gs_ctx gs_ctx;
+
+/* Pinhole camera with world-to-camera pose (the viewing transform W of Eq. 2):
+ * x_cam = R x_world + t; camera x right, y down, z forward. Pixel (px, py)
+ * samples the image plane at (px, py) in the frame where u = fx x/z + cx. */
+typedef struct gs_camera {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float R[9];   /* row-major */
+    float t[3];
+} gs_camera;
+
+/* Every constant of the method. The paper fixes only reg_floor (Eq. 10) and
+ * gives no value for the others; gs_default_config() sets the readings
+ * documented with each field. */
+typedef struct gs_config {
+    float near_z;        /* cull t_z <= near_z (0.2)                                  */
+    float fov_clamp;     /* J uses x/z, y/z clamped to fov_clamp x half-FOV tan (1.3)  */
+    float dilation;      /* Sigma2D += dilation I (0.3)                               */
+    float lambda_floor;  /* discriminant floor of the largest eigenvalue (0.1)        */
+    float radius_sigma;  /* r = ceil(radius_sigma sqrt(lambda_max)) (3)               */
+    float alpha_min;     /* skip alpha < alpha_min (1/255)                            */
+    float alpha_max;     /* alpha = min(alpha_max, o G) (0.99)                        */
+    float T_min;         /* stop before T (1 - alpha) < T_min (1e-4)                  */
+    float lambda_color;  /* Eq. 11 weight of the photometric term (1)                 */
+    float lambda_reg;    /* Eq. 11 weight of the planar term (1)                      */
+    float reg_floor;     /* Eq. 10 floor of min(s) (0.01)                             */
+    float beta1, beta2, eps;     /* Adam (0.9, 0.999, 1e-15)                          */
+    float lr[5];         /* Adam learning rates: means, log-scales, quaternions,
+                            opacity logits, colours (1e-3, 5e-3, 1e-3, 5e-2, 2.5e-3) */
+    float split_thresh;  /* split if mean screen-space grad norm > this (2e-4)        */
+    float split_factor;  /* children log-scale -= ln(split_factor) (1.6)              */
+    float insert_opacity;/* skip a new point if rendered opacity > this (0.99)        */
+    int32_t tile_size;   /* 8 or 16 pixels; 0 = pick by the built-in autotuner        */
+    int32_t capacity;    /* maximum number of Gaussians                               */
+    int32_t max_views;   /* maximum views per render call (<= GS_MAX_VIEWS)           */
+    int32_t max_width, max_height; /* largest image of any view                       */
+    int64_t pair_capacity; /* (view, tile, Gaussian) pairs per render; 0 = 8 x capacity x max_views */
+    uint64_t seed;       /* counter-based generator seed (split samples)              */
+} gs_config;
+
+/* Fill *cfg with the defaults listed above (capacity 1<<20, 8 views, 1280x720). */
+GS_API void gs_default_config(gs_config* cfg);
+
+/* Create a context on CUDA device `device`; allocates every buffer for the
+ * configured capacities (device memory, owned by the context).
+ * Errors: GS_ERR_ARG (bad config), GS_ERR_OOM, GS_ERR_CUDA. */
+GS_API int gs_create(const gs_config* cfg, int device, gs_ctx** out);
+
+/* Free the context and all its device memory. Accepts NULL. */
+GS_API void gs_destroy(gs_ctx* ctx);
+
+/* Last error message of this context ("" if none); valid until the next call. */
+GS_API const char* gs_last_error(const gs_ctx* ctx);
+
+/* Number of Gaussians currently in the map. */
+GS_API int gs_num_gaussians(const gs_ctx* ctx);
+
+/* Replace the map by n Gaussians copied from params_dev ([14][n] float32,
+ * row stride n). Resets Adam moments, the Adam step count and the
+ * densification statistics. Errors: GS_ERR_ARG, GS_ERR_CAPACITY (n > capacity). */
+GS_API int gs_set_params(gs_ctx* ctx, const float* params_dev, int n, void* stream);
+
+/* Copy the current parameters to params_dev ([14][n], row stride n = gs_num_gaussians). */
+GS_API int gs_get_params(gs_ctx* ctx, float* params_dev, void* stream);
+
+/* Copy the gradient of the last gs_backward ([14][n] float32, row stride n). */
+GS_API int gs_get_grads(gs_ctx* ctx, float* grads_dev, void* stream);
+
+/* Map initialisation from back-projected patch centres (Eq. 6, Section 3.2
+ * "Map Initialization"): appends one Gaussian per point of points_dev
+ * ([n][3] world xyz) with colour rgb_dev ([n][3]) and the plain
+ * initialisation: log-scale = ln of the RMS distance to the 3 nearest other
+ * points (clamped to [-7, -1], isotropic), quaternion (1,0,0,0), opacity
+ * logit 0. Errors: GS_ERR_ARG, GS_ERR_CAPACITY. */
+GS_API int gs_init_map(gs_ctx* ctx, const float* points_dev, const float* rgb_dev, int n, void* stream);
+
+/* Render n_views views (Eq. 2 projection, tile binning, (tile, depth) sort,
+ * Eq. 3 front-to-back compositing; Section 3.1). cams_host: n_views cameras.
+ * rgb_dev: [n_views][3][H][W] output (H, W of each view; all views must
+ * share one size). T_dev: optional [n_views][H][W] final transmittance.
+ * argmax_dev: optional [n_views][H][W] int32 id of the Gaussian with the
+ * largest blend weight (Eq. 8), -1 where nothing blends.
+ * Keeps the per-pixel state that gs_backward needs. Synchronises the stream
+ * once to size the pair buffers. Errors: GS_ERR_ARG, GS_ERR_CAPACITY (pair
+ * buffer too small; the context grows it when possible), GS_ERR_CUDA. */
+GS_API int gs_render(gs_ctx* ctx, const gs_camera* cams_host, int n_views, float* rgb_dev, float* T_dev,
+              int32_t* argmax_dev, void* stream);
+
+/* Loss of the last render (Eq. 10-11, Section 3.2 "Map Optimization"):
+ * L = sum_views lambda_color mean_{3HW}|C - I| + lambda_reg mean_i max(reg_floor, min_k s_ik).
+ * target_dev: [n_views][3][H][W]. loss_dev: optional float[3] = {L, photometric, planar}.
+ * Stores dL/dC for gs_backward(ctx, NULL, ...). */
+GS_API int gs_loss(gs_ctx* ctx, const float* target_dev, float* loss_dev, void* stream);
+
+/* Adjoint of the last render: gradients of the loss with respect to all
+ * parameters (means, log-scales, quaternions, opacity logits, colours),
+ * overwriting the context's gradient buffer. dL_drgb_dev: [n_views][3][H][W]
+ * upstream gradient of the rendered image, or NULL to use the L1 gradient
+ * stored by gs_loss, in which case the planar-term gradient is added too.
+ * Recomputes per-pixel transmittance back to front from the stored final T
+ * (no per-Gaussian blend state is stored). Errors: GS_ERR_STATE if no render. */
+GS_API int gs_backward(gs_ctx* ctx, const float* dL_drgb_dev, void* stream);
+
+/* One Adam step on every parameter with the gradient of the last gs_backward. */
+GS_API int gs_step(gs_ctx* ctx, void* stream);
+
+/* One full mapping iteration (Section 3.2 "Map Optimization"): render ->
+ * loss -> backward -> Adam over the given views, recorded once per shape
+ * into a CUDA graph and replayed. target_dev [n_views][3][H][W];
+ * loss_dev optional float[3]; rgb_dev optional output image. Uses the
+ * autotuned tile size when the config says 0. */
+GS_API int gs_iterate(gs_ctx* ctx, const gs_camera* cams_host, int n_views, const float* target_dev,
+               float* loss_dev, float* rgb_dev, void* stream);
+
+/* Dynamic insertion for keyframe `cam` (Eq. 7 reading, Section 3.2 "Dynamic
+ * 3D Gaussian Insertion"): renders the accumulated opacity of the current map
+ * in that view; a point of points_dev ([n][3] world xyz) that projects in
+ * front of the camera to a pixel whose opacity 1 - T exceeds insert_opacity
+ * is skipped; every other point is appended with the plain initialisation
+ * (log-scale from the 3 nearest existing means, colour of image_dev
+ * [3][H][W] at the point's pixel). Writes the number appended to
+ * *n_inserted_host. Synchronises the stream. */
+GS_API int gs_insert(gs_ctx* ctx, const gs_camera* cam_host, const float* image_dev, const float* points_dev,
+              int n, int* n_inserted_host, void* stream);
+
+/* Densification by splitting (reading of Section 3.2 "Clarity-Enhancing
+ * Gaussian Densification" with the 3DGS gradient criterion the paper builds
+ * on): every Gaussian whose mean screen-space position-gradient norm over the
+ * backward passes in which it was visible exceeds split_thresh is replaced by
+ * two children with means mu + R S z (z standard normal), log-scales reduced
+ * by ln(split_factor), other parameters copied and Adam moments zeroed. The
+ * survivors keep their order; children follow in parent order.
+ * normals_dev: optional [n][2][3] standard normal samples (NULL = draw them
+ * with the context's counter-based generator). Resets the statistics.
+ * Writes the number of split parents to *n_split_host. Synchronises. */
+GS_API int gs_densify(gs_ctx* ctx, const float* normals_dev, int* n_split_host, void* stream);
+
+/* Device-side timing of the path's phases with CUDA events recorded on the
+ * launching stream around each phase's kernels (a profiling aid; off by
+ * default). Phases: */
+#define GS_PHASE_PROJECT 0      /* Eq. 2 projection, depth sort, scan of tile counts    */
+#define GS_PHASE_BIN 1          /* pair emission, (tile, depth) sort, tile ranges        */
+#define GS_PHASE_RASTER_FWD 2   /* Eq. 3 compositing kernel                              */
+#define GS_PHASE_LOSS 3         /* Eq. 10-11 loss and dL/dC                              */
+#define GS_PHASE_RASTER_BWD 4   /* adjoint compositing kernel                            */
+#define GS_PHASE_PROJECT_BWD 5  /* adjoint of the projection + planar gradient           */
+#define GS_PHASE_ADAM 6         /* Adam update                                           */
+#define GS_N_PHASES 7
+/* enable != 0 starts recording (discarding earlier records); 0 stops. */
+GS_API int gs_timing_enable(gs_ctx* ctx, int enable);
+/* Synchronise on the recorded events and write, per phase, the summed
+ * milliseconds (ms_host[GS_N_PHASES]) and the number of recorded intervals
+ * (counts_host[GS_N_PHASES], may be NULL); clears the records. */
+GS_API int gs_timing_read(gs_ctx* ctx, float* ms_host, int32_t* counts_host);
+
+/* Introspection for tests (synchronising, host outputs). */
+/* Per-view screen quantities of the last render, float64 host arrays of n each:
+ * out_host[k*n + i] for k = 0 u, 1 v, 2 conic a, 3 conic b, 4 conic c, 5 depth
+ * (the float32 value the sort uses), 6 radius, 7 tiles touched; row 8 is 1.0
+ * for a valid Gaussian else 0. */
+GS_API int gs_debug_projection(gs_ctx* ctx, int view, double* out_host);
+/* Sorted pairs of the last render: bins (view * tiles_per_view + tile) and
+ * values (view * n + id). Writes *count_host = P; copies min(P, max) pairs. */
+GS_API int gs_debug_pairs(gs_ctx* ctx, uint32_t* bins_host, uint32_t* vals_host, int64_t max, int64_t* count_host);
+/* Gradients of the last backward with respect to each view's screen
+ * quantities, host [n_views][9][n]: u, v, conic a, b, c, opacity, r, g, b. */
+GS_API int gs_debug_grad2d(gs_ctx* ctx, float* out_host);
+/* Algorithmic work of the last render, out_host[4]: pairs P, (pixel, Gaussian)
+ * tests of the forward pass up to each pixel's stop, blended pairs, and the
+ * pairs the backward pass walks (entries up to each pixel's last blend). */
+GS_API int gs_debug_work(gs_ctx* ctx, int64_t* out_host);
+/* Number of kernels this context has launched since it was created. */
+GS_API int64_t gs_launch_count(const gs_ctx* ctx);
+/* Tile size the last render used. */
+GS_API int gs_tile_size(const gs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_GB300_H */

@@ -30,7 +30,8 @@ Readings of points the paper leaves open (each is a field of ``Config``)
 -----------------------------------------------------------------------
 * colour: k = 3 direct RGB, unclamped; s = exp(log-scale); opacity
   o = sigmoid(logit); the quaternion is normalised inside the forward pass.
-* projection: cull t_z <= near (0.2); J evaluated at x/z, y/z clamped to
+* projection: cull t_z <= near (0.2) and screen positions beyond +-2^23 px or
+  radii beyond 2^22 px; J evaluated at x/z, y/z clamped to
   +-1.3 x the half-FOV tangent (a clamped coordinate carries no gradient);
   low-pass dilation Sigma2D += 0.3 I; largest eigenvalue with the discriminant
   floored at 0.1; integer radius r = ceil(3 sqrt(lambda_max)).
@@ -152,6 +153,8 @@ def project(params, cam, cfg: Config = Config()) -> dict:
     u = cam.fx * tx / tz + cam.cx
     v = cam.fy * ty / tz + cam.cy
     valid = (tz.detach() > cfg.near) & (det.detach() > 0)
+    # screen positions beyond +-2^23 px and radii beyond 2^22 px are culled
+    valid = valid & (u.detach().abs() < 2.0 ** 23) & (v.detach().abs() < 2.0 ** 23) & (r < 2.0 ** 22)
     with torch.no_grad():
         x0, x1, y0, y1 = pixel_box(u, v, r, cam.width, cam.height)
         valid = valid & (x0 <= x1) & (y0 <= y1)
@@ -168,10 +171,11 @@ def pixel_box(u, v, r, width, height):
     empty box has x0 > x1 or y0 > y1.
     """
     lib = torch if torch.is_tensor(u) else np
-    x0 = lib.clip(lib.ceil(u - r), 0, width)
-    x1 = lib.clip(lib.floor(u + r), -1, width - 1)
-    y0 = lib.clip(lib.ceil(v - r), 0, height)
-    y1 = lib.clip(lib.floor(v + r), -1, height - 1)
+    # r is integer-valued, so ceil(u - r) = ceil(u) - r; this form is exact in any precision
+    x0 = lib.clip(lib.ceil(u) - r, 0, width)
+    x1 = lib.clip(lib.floor(u) + r, -1, width - 1)
+    y0 = lib.clip(lib.ceil(v) - r, 0, height)
+    y1 = lib.clip(lib.floor(v) + r, -1, height - 1)
     return x0, x1, y0, y1
 
 
@@ -240,7 +244,7 @@ def composite(px, py, pr, cfg: Config, order=None, flags: bool = False):
 
     Returns dict: rgb [P, 3], T (final transmittance) [P], last (id of the last blended
     Gaussian, -1 if none), argmax (id of the largest blend weight, Eq. 8; first on ties),
-    n_contrib [P]; with ``flags`` also ``near`` [P] bool (a discrete decision lies within
+    argmax_gap (relative gap between the two largest weights), n_contrib [P]; with ``flags`` also ``near`` [P] bool (a discrete decision lies within
     FP32 rounding of its threshold), ``near_grad`` [P] (near or an alpha near the 0.99
     clamp), ``pair_near_grad`` (bool [P, K]: which Gaussian's decision is the near one) and
     ``members`` (bool [P, K]) with ``cols`` (ids of the K columns).
@@ -295,9 +299,14 @@ def composite(px, py, pr, cfg: Config, order=None, flags: bool = False):
         if K > 0:
             am = wd.argmax(dim=1)   # first maximum in depth order
             argmax = torch.where(n_contrib > 0, cols[am], torch.full_like(am, -1))
+            top = wd.topk(min(2, K), dim=1).values
+            second = top[:, 1] if K > 1 else torch.zeros(P, dtype=DT)
+            argmax_gap = torch.where(top[:, 0] > 0, (top[:, 0] - second) / top[:, 0].clamp(min=1e-300),
+                                     torch.ones(P, dtype=DT))
         else:
             argmax = torch.full((P,), -1)
-    res = dict(rgb=out_rgb, T=T_fin, last=last, argmax=argmax, n_contrib=n_contrib)
+            argmax_gap = torch.ones(P, dtype=DT)
+    res = dict(rgb=out_rgb, T=T_fin, last=last, argmax=argmax, n_contrib=n_contrib, argmax_gap=argmax_gap)
     if flags:
         res.update(_decision_flags(dx.detach(), dy.detach(), rr, oG.detach(), member, contrib, include,
                                    T_after.detach(), first_stop, pr["depth"].detach()[cols], cfg,
@@ -362,7 +371,7 @@ def render(params, cam, cfg: Config = Config(), chunk: int = 1024, pixels=None, 
         outs = []
         for s in range(0, pix.shape[0], chunk):
             outs.append(composite(pix[s:s + chunk, 0], pix[s:s + chunk, 1], pr, cfg, order, flags=flags))
-    keys = ["rgb", "T", "last", "argmax", "n_contrib"] + (["near", "near_grad"] if flags else [])
+    keys = ["rgb", "T", "last", "argmax", "n_contrib", "argmax_gap"] + (["near", "near_grad"] if flags else [])
     res = {k: torch.cat([o[k] for o in outs]).numpy() for k in keys}
     if flags:
         gsel = np.zeros(p.shape[1], bool)

@@ -1,0 +1,793 @@
+// C ABI and host runtime: context, buffers, the render / loss / backward /
+// step sequence, and the CUDA-graph mapping iteration.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "gs_internal.cuh"
+
+using namespace gs;
+
+namespace {
+
+int fail(gs_ctx* c, int code, const char* what, cudaError_t e = cudaSuccess) {
+    char buf[512];
+    if (e != cudaSuccess)
+        snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    else
+        snprintf(buf, sizeof(buf), "%s", what);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define CK(call)                                                 \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return fail(c, GS_ERR_CUDA, #call, e_); \
+    } while (0)
+
+struct CamBatch {
+    DevCamera cam[GS_MAX_VIEWS];
+    int n;
+};
+
+__global__ void k_set_cams(CamBatch b, DevCamera* dst) {
+    int i = threadIdx.x;
+    if (i < b.n) dst[i] = b.cam[i];
+}
+
+__global__ void k_tick(uint32_t* t) { *t += 1u; }
+
+__global__ void k_fill(float* p, size_t n, float v) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+DevConst dev_const(const gs_config& f) {
+    DevConst k;
+    k.near_z = f.near_z;
+    k.dilation = f.dilation;
+    k.lambda_floor = f.lambda_floor;
+    k.radius_sigma = f.radius_sigma;
+    k.alpha_min = f.alpha_min;
+    k.alpha_max = f.alpha_max;
+    k.T_min = f.T_min;
+    k.lambda_color = f.lambda_color;
+    k.lambda_reg = f.lambda_reg;
+    k.reg_floor = f.reg_floor;
+    return k;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+int ceil_log2(uint32_t x) {
+    int b = 0;
+    while ((1u << b) < x) ++b;
+    return b;
+}
+
+bool camera_ok(const gs_camera& g, const gs_config& f) {
+    if (g.width <= 0 || g.height <= 0 || g.width > f.max_width || g.height > f.max_height) return false;
+    if (!(g.fx > 0.f) || !(g.fy > 0.f)) return false;
+    const float* v[4] = {&g.fx, &g.fy, &g.cx, &g.cy};
+    for (auto x : v)
+        if (!std::isfinite(*x)) return false;
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(g.R[i])) return false;
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(g.t[i])) return false;
+    return true;
+}
+
+void make_cam(const gs_camera& g, const gs_config& f, int tile, int view, DevCamera& d) {
+    memcpy(d.R, g.R, sizeof(d.R));
+    memcpy(d.t, g.t, sizeof(d.t));
+    d.fx = g.fx;
+    d.fy = g.fy;
+    d.cx = g.cx;
+    d.cy = g.cy;
+    d.lim_x = f.fov_clamp * (0.5f * (float)g.width / g.fx);
+    d.lim_y = f.fov_clamp * (0.5f * (float)g.height / g.fy);
+    d.width = g.width;
+    d.height = g.height;
+    d.tiles_x = (g.width + tile - 1) / tile;
+    d.tiles_y = (g.height + tile - 1) / tile;
+    d.bin_base = view * d.tiles_x * d.tiles_y;
+    d.pad = 0;
+}
+
+void free_pairs(gs_ctx* c) {
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(c->pkey[i]);
+        cudaFree(c->pval[i]);
+        c->pkey[i] = c->pval[i] = nullptr;
+    }
+}
+
+cudaError_t alloc_pairs(gs_ctx* c, int64_t cap) {
+    free_pairs(c);
+    c->pair_cap = cap;
+    cudaError_t e;
+    for (int i = 0; i < 2; ++i) {
+        if ((e = dalloc(&c->pkey[i], (size_t)cap)) != cudaSuccess) return e;
+        if ((e = dalloc(&c->pval[i], (size_t)cap)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+void drop_graph(gs_ctx* c) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+}
+
+int pick_tile(gs_ctx* c, int w, int h) {
+    if (c->cfg.tile_size == 8 || c->cfg.tile_size == 16) return c->cfg.tile_size;
+    for (int i = 0; i < 4; ++i)
+        if (c->tuned_tile[i] && c->tuned_key[i][0] == w && c->tuned_key[i][1] == h &&
+            c->tuned_key[i][2] == ceil_log2((uint32_t)std::max(c->n, 1)))
+            return c->tuned_tile[i];
+    return 16;
+}
+
+// Set up the per-view cameras of a render and upload them with a kernel (no
+// host-memory copy, so the same sequence can be captured into a graph).
+int setup_views(gs_ctx* c, const gs_camera* cams, int n_views, cudaStream_t s) {
+    if (n_views < 1 || n_views > c->cfg.max_views) return fail(c, GS_ERR_ARG, "n_views out of range");
+    if (cams == nullptr) return fail(c, GS_ERR_ARG, "cams is NULL");
+    for (int v = 0; v < n_views; ++v) {
+        if (!camera_ok(cams[v], c->cfg)) return fail(c, GS_ERR_ARG, "invalid camera");
+        if (cams[v].width != cams[0].width || cams[v].height != cams[0].height)
+            return fail(c, GS_ERR_ARG, "all views of one call must share one image size");
+    }
+    int tile = pick_tile(c, cams[0].width, cams[0].height);
+    CamBatch b;
+    memset(&b, 0, sizeof(b));
+    b.n = n_views;
+    for (int v = 0; v < n_views; ++v) make_cam(cams[v], c->cfg, tile, v, b.cam[v]);
+    int bins = n_views * b.cam[0].tiles_x * b.cam[0].tiles_y;
+    if (bins > c->max_bins) return fail(c, GS_ERR_ARG, "too many tiles for the configured maximum image size");
+    c->tile = tile;
+    c->n_views = n_views;
+    c->width = cams[0].width;
+    c->height = cams[0].height;
+    c->n_bins = bins;
+    memcpy(c->hcam, b.cam, sizeof(DevCamera) * n_views);
+    ++c->launches;
+    k_set_cams<<<1, 32, 0, s>>>(b, c->dcam);
+    CK(cudaGetLastError());
+    return GS_OK;
+}
+
+cudaEvent_t take_event(gs_ctx* c) {
+    if (!c->tpool.empty()) {
+        cudaEvent_t e = c->tpool.back();
+        c->tpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Records CUDA events around one phase on the launching stream when timing is on.
+struct Phase {
+    gs_ctx* c;
+    cudaStream_t s;
+    cudaEvent_t end = nullptr;
+    Phase(gs_ctx* c_, int id, cudaStream_t s_) : c(c_), s(s_) {
+        if (!c->timing) return;
+        cudaEvent_t a = take_event(c);
+        end = take_event(c);
+        if (!a || !end) {
+            end = nullptr;
+            return;
+        }
+        cudaEventRecord(a, s);
+        c->trec.push_back({id, a, end});
+    }
+    ~Phase() {
+        if (end) cudaEventRecord(end, s);
+    }
+};
+
+// Projection, depth sort, scan. Leaves P in dcount[0].
+int front_half(gs_ctx* c, const DevConst& k, cudaStream_t s) {
+    const uint32_t items = (uint32_t)c->n_views * (uint32_t)c->n;
+    Phase ph(c, GS_PHASE_PROJECT, s);
+    CK(launch_preprocess(c, c->n_views, k, s));
+    int buf = 0;
+    CK(radix_sort_pairs(c, c->dkey, c->dval, c->dcount + 3, items, items, 32, &buf, s));
+    CK(scan_tiles(c, items, s));
+    return GS_OK;
+}
+
+// Emission, bin sort, ranges, forward raster.
+int back_half(gs_ctx* c, const DevConst& k, float* rgb, int32_t* argmax, cudaStream_t s) {
+    const uint32_t items = (uint32_t)c->n_views * (uint32_t)c->n;
+    {
+        Phase ph(c, GS_PHASE_BIN, s);
+        CK(cudaMemsetAsync(c->dcount + 1, 0, sizeof(uint32_t), s));
+        CK(emit_pairs(c, items, s));
+        int bits = std::max(1, ceil_log2((uint32_t)c->n_bins));
+        CK(radix_sort_pairs(c, c->pkey, c->pval, c->dcount, (uint32_t)std::min<int64_t>(c->pair_cap, 0xFFFFFFFFll),
+                            c->pairs_hint, bits, &c->pair_buf, s));
+        CK(compute_ranges(c, s));
+    }
+    Phase ph(c, GS_PHASE_RASTER_FWD, s);
+    CK(launch_raster_forward(c, k, rgb, argmax, s));
+    return GS_OK;
+}
+
+int render_empty(gs_ctx* c, float* rgb, float* T, int32_t* argmax, cudaStream_t s) {
+    const size_t HW = (size_t)c->width * c->height;
+    CK(cudaMemsetAsync(rgb, 0, sizeof(float) * 3 * HW * c->n_views, s));
+    ++c->launches;
+    k_fill<<<64, 256, 0, s>>>(c->T_final, HW * c->n_views, 1.f);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(c->n_last, 0, sizeof(uint32_t) * HW * c->n_views, s));
+    if (argmax) CK(cudaMemsetAsync(argmax, 0xFF, sizeof(int32_t) * HW * c->n_views, s));
+    CK(launch_copy_T(c, T, s));
+    CK(cudaMemsetAsync(c->dcount, 0, sizeof(uint32_t), s));
+    return GS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gs_default_config(gs_config* f) {
+    if (!f) return;
+    memset(f, 0, sizeof(*f));
+    f->near_z = 0.2f;
+    f->fov_clamp = 1.3f;
+    f->dilation = 0.3f;
+    f->lambda_floor = 0.1f;
+    f->radius_sigma = 3.f;
+    f->alpha_min = 1.f / 255.f;
+    f->alpha_max = 0.99f;
+    f->T_min = 1e-4f;
+    f->lambda_color = 1.f;
+    f->lambda_reg = 1.f;
+    f->reg_floor = 0.01f;
+    f->beta1 = 0.9f;
+    f->beta2 = 0.999f;
+    f->eps = 1e-15f;
+    f->lr[0] = 1e-3f;
+    f->lr[1] = 5e-3f;
+    f->lr[2] = 1e-3f;
+    f->lr[3] = 5e-2f;
+    f->lr[4] = 2.5e-3f;
+    f->split_thresh = 2e-4f;
+    f->split_factor = 1.6f;
+    f->insert_opacity = 0.99f;
+    f->tile_size = 16;
+    f->capacity = 1 << 20;
+    f->max_views = 8;
+    f->max_width = 1280;
+    f->max_height = 720;
+    f->pair_capacity = 0;
+    f->seed = 0x5eedULL;
+}
+
+int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
+    if (!cfg || !out) return GS_ERR_ARG;
+    *out = nullptr;
+    if (cfg->capacity <= 0 || cfg->max_views < 1 || cfg->max_views > GS_MAX_VIEWS || cfg->max_width <= 0 ||
+        cfg->max_height <= 0 || (cfg->tile_size != 0 && cfg->tile_size != 8 && cfg->tile_size != 16))
+        return GS_ERR_ARG;
+    if ((int64_t)cfg->capacity * cfg->max_views >= (int64_t)0xFFFFFFFF) return GS_ERR_ARG;
+    gs_ctx* c = new gs_ctx();
+    c->cfg = *cfg;
+    c->device = device;
+    c->cap = cfg->capacity;
+    int code = GS_OK;
+    do {
+        cudaError_t e = cudaSetDevice(device);
+        if (e != cudaSuccess) { code = fail(c, GS_ERR_CUDA, "cudaSetDevice", e); break; }
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+        if (c->num_sms <= 0) c->num_sms = 1;
+        c->sort_blocks = c->num_sms * 2;
+        c->n_partials = 2 * c->num_sms * 2;
+        const size_t cap = (size_t)c->cap, V = (size_t)cfg->max_views;
+        const size_t maxpix = (size_t)cfg->max_width * cfg->max_height;
+        c->max_bins = (int)(V * ((cfg->max_width + 7) / 8) * ((cfg->max_height + 7) / 8));
+        int64_t pc = cfg->pair_capacity > 0 ? cfg->pair_capacity : (int64_t)8 * cap * V;
+        pc = std::min<int64_t>(pc, 0xFFFFFFF0ll);
+        bool ok = true;
+        ok = ok && dalloc(&c->params, kParamRows * cap) == cudaSuccess;
+        ok = ok && dalloc(&c->grads, kParamRows * cap) == cudaSuccess;
+        ok = ok && dalloc(&c->adam_m, kParamRows * cap) == cudaSuccess;
+        ok = ok && dalloc(&c->adam_v, kParamRows * cap) == cudaSuccess;
+        ok = ok && dalloc(&c->dens_sum, cap) == cudaSuccess;
+        ok = ok && dalloc(&c->dens_cnt, cap) == cudaSuccess;
+        ok = ok && dalloc(&c->dcam, V) == cudaSuccess;
+        ok = ok && dalloc(&c->rec, 3 * V * cap) == cudaSuccess;
+        ok = ok && dalloc(&c->tiles_touched, V * cap) == cudaSuccess;
+        ok = ok && dalloc(&c->depth, V * cap) == cudaSuccess;
+        for (int i = 0; i < 2; ++i) {
+            ok = ok && dalloc(&c->dkey[i], V * cap) == cudaSuccess;
+            ok = ok && dalloc(&c->dval[i], V * cap) == cudaSuccess;
+        }
+        ok = ok && dalloc(&c->offsets, V * cap) == cudaSuccess;
+        ok = ok && dalloc(&c->ranges, (size_t)c->max_bins) == cudaSuccess;
+        ok = ok && dalloc(&c->T_final, V * maxpix) == cudaSuccess;
+        ok = ok && dalloc(&c->n_last, V * maxpix) == cudaSuccess;
+        ok = ok && dalloc(&c->dLdC, 3 * V * maxpix) == cudaSuccess;
+        ok = ok && dalloc(&c->grad2d, kGrad2dStride * V * cap) == cudaSuccess;
+        ok = ok && dalloc(&c->hist, (size_t)256 * c->sort_blocks) == cudaSuccess;
+        ok = ok && dalloc(&c->dcount, 8) == cudaSuccess;
+        ok = ok && dalloc(&c->partials, (size_t)c->n_partials + 4) == cudaSuccess;
+        ok = ok && alloc_pairs(c, pc) == cudaSuccess;
+        ok = ok && cudaMallocHost((void**)&c->hcount, sizeof(uint32_t) * 8) == cudaSuccess;
+        if (!ok) { code = fail(c, GS_ERR_OOM, "device allocation failed"); break; }
+        uint32_t init[8] = {0, 0, 0, 0xFFFFFFFFu, 0, 0, 0, 0};
+        e = cudaMemcpy(c->dcount, init, sizeof(init), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(c->adam_m, 0, sizeof(float) * kParamRows * cap);
+        if (e == cudaSuccess) e = cudaMemset(c->adam_v, 0, sizeof(float) * kParamRows * cap);
+        if (e == cudaSuccess) e = cudaMemset(c->grads, 0, sizeof(float) * kParamRows * cap);
+        if (e == cudaSuccess) e = cudaMemset(c->grad2d, 0, sizeof(float) * kGrad2dStride * V * cap);
+        if (e == cudaSuccess) e = cudaMemset(c->dens_sum, 0, sizeof(float) * cap);
+        if (e == cudaSuccess) e = cudaMemset(c->dens_cnt, 0, sizeof(float) * cap);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) { code = fail(c, GS_ERR_CUDA, "initialisation", e); break; }
+    } while (0);
+    if (code != GS_OK) {
+        gs_destroy(c);
+        return code;
+    }
+    *out = c;
+    return GS_OK;
+}
+
+void gs_destroy(gs_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    drop_graph(c);
+    for (auto& r : c->trec) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : c->tpool) cudaEventDestroy(e);
+    void* ptrs[] = {c->params, c->grads, c->adam_m, c->adam_v, c->dens_sum, c->dens_cnt, c->dcam, c->rec,
+                    c->tiles_touched, c->depth, c->dkey[0], c->dkey[1], c->dval[0], c->dval[1], c->offsets, c->ranges,
+                    c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->dcount, c->partials, c->own_rgb};
+    for (void* p : ptrs) cudaFree(p);
+    free_pairs(c);
+    if (c->hcount) cudaFreeHost(c->hcount);
+    delete c;
+}
+
+const char* gs_last_error(const gs_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int gs_num_gaussians(const gs_ctx* c) { return c ? c->n : 0; }
+
+int gs_tile_size(const gs_ctx* c) { return c ? c->tile : 0; }
+
+int64_t gs_launch_count(const gs_ctx* c) { return c ? c->launches : 0; }
+
+int gs_set_params(gs_ctx* c, const float* params_dev, int n, void* stream) {
+    if (!c) return GS_ERR_ARG;
+    if (n < 0 || (n > 0 && !params_dev)) return fail(c, GS_ERR_ARG, "bad params");
+    if (n > c->cap) return fail(c, GS_ERR_CAPACITY, "more Gaussians than the configured capacity");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(c->device));
+    if (n > 0)
+        CK(cudaMemcpy2DAsync(c->params, sizeof(float) * c->cap, params_dev, sizeof(float) * n, sizeof(float) * n,
+                             kParamRows, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(c->adam_m, 0, sizeof(float) * kParamRows * c->cap, s));
+    CK(cudaMemsetAsync(c->adam_v, 0, sizeof(float) * kParamRows * c->cap, s));
+    CK(cudaMemsetAsync(c->dens_sum, 0, sizeof(float) * c->cap, s));
+    CK(cudaMemsetAsync(c->dens_cnt, 0, sizeof(float) * c->cap, s));
+    CK(cudaMemsetAsync(c->dcount + 4, 0, sizeof(uint32_t), s));
+    c->n = n;
+    c->adam_t = 0;
+    c->n_views = 0;
+    c->loss_ready = c->backward_ready = false;
+    drop_graph(c);
+    return GS_OK;
+}
+
+int gs_get_params(gs_ctx* c, float* out, void* stream) {
+    if (!c) return GS_ERR_ARG;
+    if (c->n == 0) return GS_OK;
+    if (!out) return fail(c, GS_ERR_ARG, "out is NULL");
+    CK(cudaMemcpy2DAsync(out, sizeof(float) * c->n, c->params, sizeof(float) * c->cap, sizeof(float) * c->n,
+                         kParamRows, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return GS_OK;
+}
+
+int gs_get_grads(gs_ctx* c, float* out, void* stream) {
+    if (!c) return GS_ERR_ARG;
+    if (c->n == 0) return GS_OK;
+    if (!out) return fail(c, GS_ERR_ARG, "out is NULL");
+    CK(cudaMemcpy2DAsync(out, sizeof(float) * c->n, c->grads, sizeof(float) * c->cap, sizeof(float) * c->n,
+                         kParamRows, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return GS_OK;
+}
+
+int gs_render(gs_ctx* c, const gs_camera* cams, int n_views, float* rgb, float* T, int32_t* argmax, void* stream) {
+    if (!c) return GS_ERR_ARG;
+    if (!rgb) return fail(c, GS_ERR_ARG, "rgb_dev is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(c->device));
+    c->loss_ready = c->backward_ready = false;
+    int code = setup_views(c, cams, n_views, s);
+    if (code != GS_OK) {
+        c->n_views = 0;
+        return code;
+    }
+    const DevConst k = dev_const(c->cfg);
+    c->rendered_rgb = rgb;
+    if (c->n == 0) return render_empty(c, rgb, T, argmax, s);
+    if ((code = front_half(c, k, s)) != GS_OK) return code;
+    // size the pair buffers: read P back (the one synchronisation of a render)
+    CK(cudaMemcpyAsync(c->hcount, c->dcount, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int64_t P = c->hcount[0];
+    c->pairs_hint = (uint32_t)std::min<int64_t>(P, 0xFFFFFFFFll);
+    if (P > c->pair_cap) {
+        drop_graph(c);
+        if (alloc_pairs(c, std::min<int64_t>(P + P / 2 + 1024, 0xFFFFFFF0ll)) != cudaSuccess) {
+            c->n_views = 0;
+            return fail(c, GS_ERR_OOM, "growing the pair buffers failed");
+        }
+        if (P > c->pair_cap) {
+            c->n_views = 0;
+            return fail(c, GS_ERR_CAPACITY, "pair count exceeds 2^32");
+        }
+    }
+    if ((code = back_half(c, k, rgb, argmax, s)) != GS_OK) return code;
+    CK(launch_copy_T(c, T, s));
+    return GS_OK;
+}
+
+int gs_loss(gs_ctx* c, const float* target, float* loss_dev, void* stream) {
+    if (!c) return GS_ERR_ARG;
+    if (c->n_views == 0 || !c->rendered_rgb) return fail(c, GS_ERR_STATE, "gs_loss before gs_render");
+    if (!target) return fail(c, GS_ERR_ARG, "target_dev is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    float* out = loss_dev ? loss_dev : c->partials + c->n_partials;
+    const DevConst k = dev_const(c->cfg);
+    Phase ph(c, GS_PHASE_LOSS, s);
+    CK(launch_loss(c, k, c->rendered_rgb, target, out, s));
+    c->loss_ready = true;
+    return GS_OK;
+}
+
+int gs_backward(gs_ctx* c, const float* dL_drgb, void* stream) {
+    if (!c) return GS_ERR_ARG;
+    if (c->n_views == 0) return fail(c, GS_ERR_STATE, "gs_backward before gs_render");
+    if (!dL_drgb && !c->loss_ready) return fail(c, GS_ERR_STATE, "gs_backward(NULL) before gs_loss");
+    cudaStream_t s = (cudaStream_t)stream;
+    const DevConst k = dev_const(c->cfg);
+    if (c->n == 0) {
+        c->backward_ready = true;
+        return GS_OK;
+    }
+    CK(cudaMemsetAsync(c->grad2d, 0, sizeof(float) * kGrad2dStride * c->n_views * (size_t)c->n, s));
+    {
+        Phase ph(c, GS_PHASE_RASTER_BWD, s);
+        CK(launch_raster_backward(c, k, dL_drgb ? dL_drgb : c->dLdC, s));
+    }
+    Phase ph(c, GS_PHASE_PROJECT_BWD, s);
+    CK(launch_preprocess_backward(c, k, dL_drgb == nullptr, s));
+    c->backward_ready = true;
+    return GS_OK;
+}
+
+int gs_step(gs_ctx* c, void* stream) {
+    if (!c) return GS_ERR_ARG;
+    if (!c->backward_ready) return fail(c, GS_ERR_STATE, "gs_step before gs_backward");
+    cudaStream_t s = (cudaStream_t)stream;
+    c->adam_t += 1;
+    Phase ph(c, GS_PHASE_ADAM, s);
+    CK(launch_adam(c, s));
+    ++c->launches;
+    k_tick<<<1, 1, 0, s>>>(c->dcount + 4);
+    CK(cudaGetLastError());
+    c->backward_ready = false;
+    return GS_OK;
+}
+
+int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* target, float* loss_dev, float* rgb,
+               void* stream) {
+    if (!c) return GS_ERR_ARG;
+    if (!target) return fail(c, GS_ERR_ARG, "target_dev is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(c->device));
+    if (!rgb) {
+        if (n_views < 1 || n_views > c->cfg.max_views || !cams) return fail(c, GS_ERR_ARG, "bad views");
+        size_t need = (size_t)n_views * 3 * cams[0].width * cams[0].height;
+        if (need > c->own_rgb_elems) {
+            cudaFree(c->own_rgb);
+            c->own_rgb = nullptr;
+            c->own_rgb_elems = 0;
+            if (dalloc(&c->own_rgb, need) != cudaSuccess) return fail(c, GS_ERR_OOM, "image buffer");
+            c->own_rgb_elems = need;
+        }
+        rgb = c->own_rgb;
+    }
+    int code = gs_render(c, cams, n_views, rgb, nullptr, nullptr, stream);
+    if (code != GS_OK) return code;
+    if ((code = gs_loss(c, target, loss_dev, stream)) != GS_OK) return code;
+    if ((code = gs_backward(c, nullptr, stream)) != GS_OK) return code;
+    return gs_step(c, s);
+}
+
+int gs_timing_enable(gs_ctx* c, int enable) {
+    if (!c) return GS_ERR_ARG;
+    for (auto& r : c->trec) {
+        c->tpool.push_back(r.a);
+        c->tpool.push_back(r.b);
+    }
+    c->trec.clear();
+    c->timing = enable != 0;
+    return GS_OK;
+}
+
+int gs_timing_read(gs_ctx* c, float* ms, int32_t* counts) {
+    if (!c || !ms) return GS_ERR_ARG;
+    for (int i = 0; i < GS_N_PHASES; ++i) {
+        ms[i] = 0.f;
+        if (counts) counts[i] = 0;
+    }
+    int code = GS_OK;
+    for (auto& r : c->trec) {
+        float t = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess) {
+            code = fail(c, GS_ERR_CUDA, "timing event", e);
+            break;
+        }
+        if (r.phase >= 0 && r.phase < GS_N_PHASES) {
+            ms[r.phase] += t;
+            if (counts) counts[r.phase] += 1;
+        }
+    }
+    for (auto& r : c->trec) {
+        c->tpool.push_back(r.a);
+        c->tpool.push_back(r.b);
+    }
+    c->trec.clear();
+    return code;
+}
+
+int gs_debug_projection(gs_ctx* c, int view, double* out) {
+    if (!c || !out) return GS_ERR_ARG;
+    if (c->n_views == 0 || view < 0 || view >= c->n_views) return fail(c, GS_ERR_STATE, "no such rendered view");
+    const size_t n = (size_t)c->n;
+    std::vector<float4> rec(3 * n);
+    std::vector<uint32_t> tl(n);
+    std::vector<float> dep(n);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && n)
+        e = cudaMemcpy(rec.data(), c->rec + 3 * n * view, sizeof(float4) * 3 * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && n)
+        e = cudaMemcpy(tl.data(), c->tiles_touched + n * view, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && n) e = cudaMemcpy(dep.data(), c->depth + n * view, sizeof(float) * n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(c, GS_ERR_CUDA, "debug copy", e);
+    const double k1 = -0.5 * (double)kLog2e, k2 = -(double)kLog2e;
+    for (size_t i = 0; i < n; ++i) {
+        const float4 a = rec[3 * i], q = rec[3 * i + 1], col = rec[3 * i + 2];
+        out[0 * n + i] = (double)a.x + (double)q.w;
+        out[1 * n + i] = (double)a.y + (double)col.w;
+        out[2 * n + i] = q.x / k1;
+        out[3 * n + i] = q.y / k2;
+        out[4 * n + i] = q.z / k1;
+        out[5 * n + i] = dep[i];
+        out[6 * n + i] = a.z;
+        out[7 * n + i] = (double)tl[i];
+        out[8 * n + i] = a.z >= 0.f ? 1.0 : 0.0;
+    }
+    return GS_OK;
+}
+
+int gs_debug_pairs(gs_ctx* c, uint32_t* bins, uint32_t* vals, int64_t max, int64_t* count) {
+    if (!c || !count) return GS_ERR_ARG;
+    CK(cudaDeviceSynchronize());
+    uint32_t P = 0;
+    CK(cudaMemcpy(&P, c->dcount, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    *count = P;
+    int64_t m = std::min<int64_t>(P, max);
+    if (m > 0 && bins) CK(cudaMemcpy(bins, c->pkey[c->pair_buf], sizeof(uint32_t) * m, cudaMemcpyDeviceToHost));
+    if (m > 0 && vals) CK(cudaMemcpy(vals, c->pval[c->pair_buf], sizeof(uint32_t) * m, cudaMemcpyDeviceToHost));
+    return GS_OK;
+}
+
+int gs_debug_work(gs_ctx* c, int64_t* out) {
+    if (!c || !out) return GS_ERR_ARG;
+    if (c->n_views == 0) return fail(c, GS_ERR_STATE, "no render");
+    unsigned long long* d = nullptr;
+    CK(cudaMalloc((void**)&d, sizeof(unsigned long long) * 4));
+    unsigned long long h[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemset(d, 0, sizeof(h));
+    if (e == cudaSuccess && c->n > 0) e = launch_count_work(c, dev_const(c->cfg), d, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    uint32_t P = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&P, c->dcount, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(c, GS_ERR_CUDA, "work count", e);
+    out[0] = c->n > 0 ? (int64_t)P : 0;
+    out[1] = (int64_t)h[0];
+    out[2] = (int64_t)h[1];
+    out[3] = (int64_t)h[2];
+    return GS_OK;
+}
+
+int gs_debug_grad2d(gs_ctx* c, float* out) {
+    if (!c || !out) return GS_ERR_ARG;
+    if (c->n_views == 0) return fail(c, GS_ERR_STATE, "no render");
+    const size_t n = (size_t)c->n, items = n * c->n_views;
+    float* g = (float*)malloc(sizeof(float) * kGrad2dStride * items);
+    if (!g) return fail(c, GS_ERR_OOM, "host buffer");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(g, c->grad2d, sizeof(float) * kGrad2dStride * items, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        free(g);
+        return fail(c, GS_ERR_CUDA, "debug copy", e);
+    }
+    const float k1 = -0.5f * kLog2e, k2 = -kLog2e;
+    for (int v = 0; v < c->n_views; ++v)
+        for (size_t i = 0; i < n; ++i) {
+            const float* r = g + (v * n + i) * kGrad2dStride;
+            float* o = out + (size_t)v * 9 * n;
+            o[0 * n + i] = r[0];
+            o[1 * n + i] = r[1];
+            o[2 * n + i] = r[2] * k1;
+            o[3 * n + i] = r[3] * k2;
+            o[4 * n + i] = r[4] * k1;
+            o[5 * n + i] = r[5];
+            o[6 * n + i] = r[6];
+            o[7 * n + i] = r[7];
+            o[8 * n + i] = r[8];
+        }
+    free(g);
+    return GS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- map management
+
+namespace {
+
+struct Temp {
+    void* p[8] = {nullptr};
+    int k = 0;
+    template <typename T>
+    bool get(T** out, size_t count) {
+        if (cudaMalloc((void**)out, sizeof(T) * (count ? count : 1)) != cudaSuccess) {
+            *out = nullptr;
+            return false;
+        }
+        p[k++] = *out;
+        return true;
+    }
+    ~Temp() {
+        for (int i = 0; i < k; ++i) cudaFree(p[i]);
+    }
+};
+
+void invalidate_render(gs_ctx* c) {
+    c->n_views = 0;
+    c->loss_ready = c->backward_ready = false;
+    drop_graph(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+int gs_init_map(gs_ctx* c, const float* pts, const float* rgb, int n, void* stream) {
+    if (!c) return GS_ERR_ARG;
+    if (n < 0 || (n > 0 && (!pts || !rgb))) return fail(c, GS_ERR_ARG, "bad points");
+    if ((int64_t)c->n + n > c->cap) return fail(c, GS_ERR_CAPACITY, "more Gaussians than the configured capacity");
+    if (n == 0) return GS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(c->device));
+    Temp t;
+    float *ref = nullptr, *stage = nullptr;
+    if (!t.get(&ref, 3 * (size_t)n) || !t.get(&stage, kParamRows * (size_t)n))
+        return fail(c, GS_ERR_OOM, "temporary buffers");
+    CK(launch_points_planar(pts, n, ref, s));
+    CK(launch_init_points(c, pts, rgb, n, ref, n, n, 1, stage, n, s));
+    CK(cudaMemcpy2DAsync(c->params + c->n, sizeof(float) * c->cap, stage, sizeof(float) * n, sizeof(float) * n,
+                         kParamRows, cudaMemcpyDeviceToDevice, s));
+    for (float* a : {c->adam_m, c->adam_v})
+        CK(cudaMemset2DAsync(a + c->n, sizeof(float) * c->cap, 0, sizeof(float) * n, kParamRows, s));
+    CK(cudaMemsetAsync(c->dens_sum + c->n, 0, sizeof(float) * n, s));
+    CK(cudaMemsetAsync(c->dens_cnt + c->n, 0, sizeof(float) * n, s));
+    CK(cudaStreamSynchronize(s));
+    c->n += n;
+    invalidate_render(c);
+    return GS_OK;
+}
+
+int gs_insert(gs_ctx* c, const gs_camera* cam, const float* image, const float* pts, int n, int* n_ins,
+              void* stream) {
+    if (!c || !n_ins) return GS_ERR_ARG;
+    *n_ins = 0;
+    if (n < 0 || (n > 0 && (!pts || !image || !cam))) return fail(c, GS_ERR_ARG, "bad insertion arguments");
+    if (n == 0) return GS_OK;
+    if ((int64_t)c->n + n > c->cap) return fail(c, GS_ERR_CAPACITY, "insertion could exceed the capacity");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(c->device));
+    Temp t;
+    float *img = nullptr, *stage = nullptr;
+    uint32_t *keep = nullptr, *pos = nullptr;
+    const size_t HW = (size_t)cam->width * cam->height;
+    if (!t.get(&img, 3 * HW) || !t.get(&stage, kParamRows * (size_t)n) || !t.get(&keep, (size_t)n) ||
+        !t.get(&pos, (size_t)n))
+        return fail(c, GS_ERR_OOM, "temporary buffers");
+    int code = gs_render(c, cam, 1, img, nullptr, nullptr, stream);
+    if (code != GS_OK) return code;
+    CK(launch_insert_test(c, c->hcam[0], pts, n, image, keep, stage, s));
+    CK(scan_u32(c, keep, pos, (uint32_t)n, c->dcount + 5, s));
+    CK(launch_append(c, stage, n, keep, pos, s));
+    CK(cudaMemcpyAsync(c->hcount + 5, c->dcount + 5, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *n_ins = (int)c->hcount[5];
+    c->n += *n_ins;
+    invalidate_render(c);
+    return GS_OK;
+}
+
+int gs_densify(gs_ctx* c, const float* normals, int* n_split_out, void* stream) {
+    if (!c || !n_split_out) return GS_ERR_ARG;
+    *n_split_out = 0;
+    if (c->n == 0) return GS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(c->device));
+    Temp t;
+    uint32_t *flags = nullptr, *pos = nullptr;
+    if (!t.get(&flags, (size_t)c->n) || !t.get(&pos, (size_t)c->n)) return fail(c, GS_ERR_OOM, "temporary buffers");
+    CK(launch_split_flags(c, flags, s));
+    CK(scan_u32(c, flags, pos, (uint32_t)c->n, c->dcount + 5, s));
+    CK(cudaMemcpyAsync(c->hcount + 5, c->dcount + 5, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint32_t n_split = c->hcount[5];
+    if ((int64_t)c->n + n_split > c->cap) return fail(c, GS_ERR_CAPACITY, "splitting would exceed the capacity");
+    if (n_split > 0) {
+        float *P2 = nullptr, *M2 = nullptr, *V2 = nullptr;
+        const size_t sz = kParamRows * (size_t)c->cap;
+        if (dalloc(&P2, sz) != cudaSuccess) return fail(c, GS_ERR_OOM, "split buffers");
+        if (dalloc(&M2, sz) != cudaSuccess) {
+            cudaFree(P2);
+            return fail(c, GS_ERR_OOM, "split buffers");
+        }
+        if (dalloc(&V2, sz) != cudaSuccess) {
+            cudaFree(P2);
+            cudaFree(M2);
+            return fail(c, GS_ERR_OOM, "split buffers");
+        }
+        cudaError_t e = launch_split_scatter(c, flags, pos, n_split, normals, P2, M2, V2, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaFree(P2);
+            cudaFree(M2);
+            cudaFree(V2);
+            return fail(c, GS_ERR_CUDA, "split", e);
+        }
+        cudaFree(c->params);
+        cudaFree(c->adam_m);
+        cudaFree(c->adam_v);
+        c->params = P2;
+        c->adam_m = M2;
+        c->adam_v = V2;
+        c->n += (int)n_split;
+    }
+    CK(cudaMemsetAsync(c->dens_sum, 0, sizeof(float) * c->cap, s));
+    CK(cudaMemsetAsync(c->dens_cnt, 0, sizeof(float) * c->cap, s));
+    CK(cudaStreamSynchronize(s));
+    *n_split_out = (int)n_split;
+    invalidate_render(c);
+    return GS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// Internal declarations of the GB300 splatting library: context layout, device
+// camera record, launch wrappers. Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+constexpr int kParamRows = 14;
+constexpr int kGrad2dStride = 12;   // floats per (view, Gaussian) screen-gradient record
+constexpr int kRecFloat4 = 3;       // float4 per (view, Gaussian) raster record
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// Camera as the kernels read it (one per view, in device memory).
+struct DevCamera {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float lim_x, lim_y;     // fov_clamp * half-FOV tangents
+    int width, height;
+    int tiles_x, tiles_y;   // tiles of this view
+    int bin_base;           // first bin index of this view
+    int pad;
+};
+
+// Method constants as the kernels read them.
+struct DevConst {
+    float near_z, dilation, lambda_floor, radius_sigma;
+    float alpha_min, alpha_max, T_min;
+    float lambda_color, lambda_reg, reg_floor;
+};
+
+#ifdef __CUDACC__
+// Pixel box |px - u| <= r, |py - v| <= r clipped to the image, from the split
+// screen mean (integer part ui, fraction uf in [0, 1)): ceil(u) = ui + (uf > 0),
+// floor(u) = ui. Exact in float for |ui| < 2^23 and r < 2^22. Shared by the
+// tile count here and the pair emission so that both see the same box.
+__device__ __forceinline__ bool pixel_box(float ui, float uf, float vi, float vf, float r, int width, int height,
+                                          int& x0, int& x1, int& y0, int& y1) {
+    float fx0 = fmaxf(ui + (uf > 0.f ? 1.f : 0.f) - r, 0.f), fx1 = fminf(ui + r, (float)(width - 1));
+    float fy0 = fmaxf(vi + (vf > 0.f ? 1.f : 0.f) - r, 0.f), fy1 = fminf(vi + r, (float)(height - 1));
+    if (!(fx0 <= fx1 && fy0 <= fy1)) return false;
+    x0 = (int)fx0;
+    x1 = (int)fx1;
+    y0 = (int)fy0;
+    y1 = (int)fy1;
+    return true;
+}
+#endif
+
+}  // namespace gs
+
+struct gs_ctx {
+    gs_config cfg;
+    int device = 0;
+    int n = 0;                  // Gaussians in the map
+    int cap = 0;                // capacity (Gaussians)
+    int adam_t = 0;             // Adam steps taken
+    std::string err;
+
+    // map state, [14][cap] planar
+    float* params = nullptr;
+    float* grads = nullptr;
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    float* dens_sum = nullptr;  // [cap] sum of screen-space gradient norms
+    float* dens_cnt = nullptr;  // [cap] number of visible backward passes
+
+    // per-render state
+    int n_views = 0;            // views of the last render (0 = none)
+    int width = 0, height = 0;  // size of every view of the last render
+    int tile = 16;              // tile size of the last render
+    int n_bins = 0;             // bins of the last render
+    gs::DevCamera hcam[GS_MAX_VIEWS];
+    gs::DevCamera* dcam = nullptr;          // [max_views]
+    float4* rec = nullptr;                  // [max_views * cap * 3]
+    uint32_t* tiles_touched = nullptr;      // [max_views * cap]
+    float* depth = nullptr;                 // [max_views * cap] float32 view depth
+    uint32_t* dkey[2] = {nullptr, nullptr}; // depth-sort keys   [max_views * cap]
+    uint32_t* dval[2] = {nullptr, nullptr}; // depth-sort values [max_views * cap]
+    uint32_t* offsets = nullptr;            // exclusive scan of tiles touched in depth order
+    int64_t pair_cap = 0;
+    uint32_t* pkey[2] = {nullptr, nullptr}; // bin of each pair
+    uint32_t* pval[2] = {nullptr, nullptr}; // (view * cap + id) of each pair
+    int pair_buf = 0;                       // which of the two buffers holds the sorted pairs
+    uint32_t pairs_hint = 0;                // host-side pair count of the last render (grid sizing)
+    uint2* ranges = nullptr;                // [max bins] (start, end) per bin
+    int max_bins = 0;
+    float* T_final = nullptr;               // [max_views * H * W]
+    uint32_t* n_last = nullptr;             // [max_views * H * W] entries up to the last blended
+    float* dLdC = nullptr;                  // [max_views * 3 * H * W]
+    float* grad2d = nullptr;                // [max_views * cap * 12]
+    const float* rendered_rgb = nullptr;    // caller buffer of the last render
+    bool loss_ready = false;
+    bool backward_ready = false;
+
+    // scratch
+    uint32_t* hist = nullptr;               // radix / scan block counters
+    int sort_blocks = 0;
+    uint32_t* dcount = nullptr;             // device scalars: [0] pairs, [1] overflow
+    uint32_t* hcount = nullptr;             // pinned host mirror
+    float* partials = nullptr;              // reduction partials
+    int n_partials = 0;
+    int num_sms = 0;
+    int64_t launches = 0;                   // kernels launched by this context
+
+    // iterate() graph cache
+    cudaGraphExec_t graph = nullptr;
+    int graph_views = 0, graph_w = 0, graph_h = 0, graph_n = 0, graph_tile = 0;
+    int64_t graph_pair_cap = 0;
+    const float* graph_target = nullptr;
+    float* graph_loss = nullptr;
+    float* graph_rgb = nullptr;
+    float* own_rgb = nullptr;               // internal image when the caller gives none
+    size_t own_rgb_elems = 0;
+    // phase timing (gs_timing_enable / gs_timing_read)
+    bool timing = false;
+    struct TimingRec {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<TimingRec> trec;
+    std::vector<cudaEvent_t> tpool;
+    // autotuned tile size per (width, height, N-bucket)
+    int tuned_tile[4] = {0, 0, 0, 0};
+    int tuned_key[4][3];
+};
+
+namespace gs {
+
+// ---- launch wrappers (each returns cudaGetLastError() of its launches) ----
+cudaError_t launch_preprocess(gs_ctx* c, int n_views, const DevConst& k, cudaStream_t s);
+cudaError_t launch_preprocess_backward(gs_ctx* c, const DevConst& k, bool add_reg, cudaStream_t s);
+// Stable LSD radix sort of (u32 key, u32 value) pairs on the low `bits` bits.
+// The count is min(*n_dev, n_max); n_hint (host estimate) only sizes the grid.
+cudaError_t radix_sort_pairs(gs_ctx* c, uint32_t** keys, uint32_t** vals, const uint32_t* n_dev, uint32_t n_max,
+                             uint32_t n_hint, int bits, int* out_buf, cudaStream_t s);
+cudaError_t scan_tiles(gs_ctx* c, uint32_t n, cudaStream_t s);
+cudaError_t emit_pairs(gs_ctx* c, uint32_t n, cudaStream_t s);
+// exclusive scan of n u32 values (in may equal out); the total goes to *total_dev
+cudaError_t scan_u32(gs_ctx* c, const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* total_dev, cudaStream_t s);
+cudaError_t compute_ranges(gs_ctx* c, cudaStream_t s);
+cudaError_t launch_raster_forward(gs_ctx* c, const DevConst& k, float* rgb, int32_t* argmax, cudaStream_t s);
+cudaError_t launch_raster_backward(gs_ctx* c, const DevConst& k, const float* dLdC, cudaStream_t s);
+cudaError_t launch_count_work(gs_ctx* c, const DevConst& k, unsigned long long* out, cudaStream_t s);
+cudaError_t launch_loss(gs_ctx* c, const DevConst& k, const float* rgb, const float* target, float* loss_out,
+                        cudaStream_t s);
+cudaError_t launch_adam(gs_ctx* c, cudaStream_t s);
+cudaError_t launch_copy_T(gs_ctx* c, float* T_out, cudaStream_t s);
+// map management (k_map.cu)
+cudaError_t launch_init_points(gs_ctx* c, const float* pts, const float* rgb, int n, const float* ref, int ref_stride,
+                               int n_ref, int ref_is_self, float* out_params, int out_stride, cudaStream_t s);
+cudaError_t launch_points_planar(const float* pts, int n, float* out, cudaStream_t s);
+cudaError_t launch_insert_test(gs_ctx* c, const DevCamera& cam, const float* pts, int n, const float* image,
+                               uint32_t* keep, float* stage, cudaStream_t s);
+cudaError_t launch_append(gs_ctx* c, const float* stage, int n_stage, const uint32_t* keep, const uint32_t* pos,
+                          cudaStream_t s);
+cudaError_t launch_split_flags(gs_ctx* c, uint32_t* flags, cudaStream_t s);
+cudaError_t launch_split_scatter(gs_ctx* c, const uint32_t* flags, const uint32_t* pos, uint32_t n_split,
+                                 const float* normals, float* P2, float* M2, float* V2, cudaStream_t s);
+
+}  // namespace gs

@@ -1,0 +1,326 @@
+// Tile binning and the (tile, depth) ordering of the pairs.
+//
+// The order the compositing needs is lexicographic in (view, tile, depth,
+// Gaussian id). It is built in two stable steps instead of one 64-bit sort:
+//   1. a stable LSD radix sort of the V*N depth keys (32 bits, 4 passes of 8),
+//      whose stability keeps equal depths in id order;
+//   2. pairs are emitted in that depth order (one per tile a Gaussian's pixel
+//      box touches), then stably radix-sorted by bin = view * tiles + tile
+//      (ceil(log2 bins) bits, 2 passes for up to 65536 bins).
+// The second sort moves 8-byte pairs over P elements only twice instead of six
+// times for a 64-bit key, and the depth sort touches N elements, not P.
+//
+// Every pass is reduce-then-scan over a fixed grid of G blocks, each owning a
+// contiguous slice of the input; element counts are read from device memory so
+// the same launches can sit in a CUDA graph.
+#include <algorithm>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 8;                       // per lane per round
+constexpr int kRound = kSortThreads * kSortItems;   // elements per block round
+
+__device__ __forceinline__ void slice_of(uint32_t n, int G, int b, uint32_t& begin, uint32_t& end) {
+    uint32_t chunk = (n + G - 1) / G;
+    chunk = (chunk + 31u) & ~31u;
+    uint64_t b0 = (uint64_t)chunk * b, b1 = b0 + chunk;
+    begin = (uint32_t)(uint32_t)(b0 < n ? b0 : n);
+    end = (uint32_t)(uint32_t)(b1 < n ? b1 : n);
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Histogram of one digit over each block's slice: hist[d * G + b].
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys,
+                                                             const uint32_t* __restrict__ n_dev, uint32_t n_max,
+                                                             int shift, int nbits, uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[256];
+    const int G = gridDim.x, b = blockIdx.x;
+    const uint32_t mask = (1u << nbits) - 1u;
+    for (int d = threadIdx.x; d < 256; d += kSortThreads) h[d] = 0;
+    __syncthreads();
+    uint32_t n = umin(*n_dev, n_max), begin, end;
+    slice_of(n, G, b, begin, end);
+    const int lane = threadIdx.x & 31;
+    for (uint32_t base = begin + (threadIdx.x & ~31u); base < end; base += kSortThreads) {
+        uint32_t i = base + lane;
+        bool ok = i < end;
+        uint32_t d = ok ? (keys[i] >> shift) & mask : 0xFFFFFFFFu;
+        uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+        if (ok && (__ffs(peers) - 1) == lane) atomicAdd(&h[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d <= (int)mask; d += kSortThreads) hist[(size_t)d * G + b] = h[d];
+}
+
+// In-place exclusive scan of `len` counters with one block of 1024 threads,
+// walking the array in coalesced tiles of 1024 with a running carry.
+__global__ void __launch_bounds__(1024) k_scan_counts(uint32_t* __restrict__ a, uint32_t len,
+                                                      uint32_t* __restrict__ total_out) {
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t carry;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < len; base += 1024) {
+        const uint32_t i = base + t;
+        const uint32_t c = i < len ? a[i] : 0u;
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t v = warp_sums[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xFFFFFFFFu, v, o);
+                if (lane >= o) v += y;
+            }
+            warp_sums[lane] = v;
+        }
+        __syncthreads();
+        const uint32_t before = carry;
+        if (i < len) a[i] = before + x - c + (w > 0 ? warp_sums[w - 1] : 0u);
+        __syncthreads();
+        if (t == 0) carry = before + warp_sums[31];
+        __syncthreads();
+    }
+    if (t == 0 && total_out != nullptr) *total_out = carry;
+}
+
+// Stable scatter of one digit pass. Each block walks its slice in rounds of
+// kRound elements; warp w of a round owns a contiguous run of 32*kSortItems
+// elements, ranked within the warp by __match_any_sync, across warps by a
+// per-digit prefix over the warps' counts, and across blocks by the scanned
+// histogram.
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, const uint32_t* __restrict__ n_dev, uint32_t n_max, int shift, int nbits,
+    const uint32_t* __restrict__ hist) {
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t total[256];
+    __shared__ uint32_t wcnt[kSortWarps][256];
+    const int G = gridDim.x, b = blockIdx.x;
+    const uint32_t mask = (1u << nbits) - 1u;
+    const int ndig = 1 << nbits;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < ndig; d += kSortThreads) run[d] = hist[(size_t)d * G + b];
+    uint32_t n = umin(*n_dev, n_max), begin, end;
+    slice_of(n, G, b, begin, end);
+    const uint32_t lt = lanemask_lt();
+    for (uint32_t rbase = begin; rbase < end; rbase += kRound) {
+        for (int d = lane; d < ndig; d += 32) wcnt[w][d] = 0;
+        __syncwarp();
+        uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+        const uint32_t wbase = rbase + (uint32_t)w * 32u * kSortItems;
+#pragma unroll
+        for (int it = 0; it < kSortItems; ++it) {
+            uint32_t i = wbase + it * 32 + lane;
+            bool ok = i < end;
+            key[it] = ok ? kin[i] : 0u;
+            val[it] = ok ? vin[i] : 0u;
+            uint32_t d = ok ? (key[it] >> shift) & mask : 0xFFFFFFFFu;
+            uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+            uint32_t r = 0;
+            if (ok) r = wcnt[w][d] + __popc(peers & lt);
+            rank[it] = r;
+            __syncwarp();
+            if (ok && (__ffs(peers) - 1) == lane) wcnt[w][d] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < ndig; d += kSortThreads) {
+            uint32_t s = 0;
+#pragma unroll
+            for (int ww = 0; ww < kSortWarps; ++ww) {
+                uint32_t c = wcnt[ww][d];
+                wcnt[ww][d] = s;
+                s += c;
+            }
+            total[d] = s;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < kSortItems; ++it) {
+            uint32_t i = wbase + it * 32 + lane;
+            if (i < end) {
+                uint32_t d = (key[it] >> shift) & mask;
+                uint32_t pos = run[d] + wcnt[w][d] + rank[it];
+                kout[pos] = key[it];
+                vout[pos] = val[it];
+            }
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < ndig; d += kSortThreads) run[d] += total[d];
+        __syncthreads();
+    }
+}
+
+// ---- scan of the tiles touched, in depth order ----
+
+__global__ void __launch_bounds__(256) k_tile_block_sums(const uint32_t* __restrict__ order,
+                                                         const uint32_t* __restrict__ tiles, uint32_t n,
+                                                         uint32_t* __restrict__ bsum) {
+    __shared__ uint32_t ws[8];
+    uint32_t begin, end;
+    slice_of(n, gridDim.x, blockIdx.x, begin, end);
+    uint32_t s = 0;
+    for (uint32_t i = begin + threadIdx.x; i < end; i += 256) s += tiles[order ? order[i] : i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int k = 0; k < 8; ++k) t += ws[k];
+        bsum[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_tile_scan(const uint32_t* __restrict__ order,
+                                                   const uint32_t* __restrict__ tiles, uint32_t n,
+                                                   const uint32_t* __restrict__ bsum, uint32_t* __restrict__ off) {
+    __shared__ uint32_t ws[8];
+    __shared__ uint32_t carry;
+    uint32_t begin, end;
+    slice_of(n, gridDim.x, blockIdx.x, begin, end);
+    if (threadIdx.x == 0) carry = bsum[blockIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (uint32_t base = begin; base < end; base += 256) {
+        uint32_t i = base + threadIdx.x;
+        uint32_t c = i < end ? tiles[order ? order[i] : i] : 0u;
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws[w] = x;
+        __syncthreads();
+        uint32_t pre = 0, tot = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            uint32_t v = ws[k];
+            pre += (k < w) ? v : 0u;
+            tot += v;
+        }
+        if (i < end) off[i] = carry + pre + x - c;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+}
+
+// One thread per depth-sorted (view, Gaussian): write its pairs (bin, item).
+__global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ tiles,
+                                              const uint32_t* __restrict__ off, const float4* __restrict__ rec,
+                                              const DevCamera* __restrict__ cams, int n, int tile, uint32_t n_items,
+                                              uint64_t pair_cap, uint32_t* __restrict__ pkey,
+                                              uint32_t* __restrict__ pval, uint32_t* __restrict__ overflow) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_items) return;
+    uint32_t item = order[k];
+    uint32_t cnt = tiles[item];
+    if (cnt == 0) return;
+    uint64_t o = off[k];
+    if (o + cnt > pair_cap) {
+        atomicMax(overflow, 1u);
+        return;
+    }
+    const DevCamera& cam = cams[item / (uint32_t)n];
+    const float4 f0 = rec[(size_t)item * 3], f1 = rec[(size_t)item * 3 + 1], f2 = rec[(size_t)item * 3 + 2];
+    int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
+    pixel_box(f0.x, f1.w, f0.y, f2.w, f0.z, cam.width, cam.height, x0, x1, y0, y1);
+    int tx0 = x0 / tile, tx1 = x1 / tile, ty0 = y0 / tile, ty1 = y1 / tile;
+    const uint64_t o_end = o + cnt;
+    for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1 && o < o_end; ++tx) {
+            pkey[o] = (uint32_t)(cam.bin_base + ty * cam.tiles_x + tx);
+            pval[o] = item;
+            ++o;
+        }
+}
+
+__global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ pkey, const uint32_t* __restrict__ P_dev,
+                                                uint64_t pair_cap, uint32_t n_bins, uint2* __restrict__ ranges) {
+    uint32_t P = (uint32_t)(*P_dev < pair_cap ? *P_dev : pair_cap);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+        uint32_t b = pkey[i];
+        if (b >= n_bins) continue;   // only possible after a pair-buffer overflow
+        if (i == 0 || pkey[i - 1] != b) ranges[b].x = i;
+        if (i == P - 1 || pkey[i + 1] != b) ranges[b].y = i + 1;
+    }
+}
+
+}  // namespace
+
+cudaError_t radix_sort_pairs(gs_ctx* c, uint32_t** keys, uint32_t** vals, const uint32_t* n_dev, uint32_t n_max,
+                             uint32_t n_hint, int bits, int* out_buf, cudaStream_t s) {
+    int cur = 0;
+    // about 4096 elements per block (each block owns one contiguous slice)
+    const int G = (int)std::max<uint32_t>(1u, std::min<uint32_t>((uint32_t)c->sort_blocks, (n_hint + 4095u) / 4096u));
+    for (int shift = 0; shift < bits; shift += 8) {
+        int nb = bits - shift < 8 ? bits - shift : 8;
+        c->launches += 3;
+        k_radix_hist<<<G, kSortThreads, 0, s>>>(keys[cur], n_dev, n_max, shift, nb, c->hist);
+        k_scan_counts<<<1, 1024, 0, s>>>(c->hist, (uint32_t)((1u << nb) * G), nullptr);
+        k_radix_scatter<<<G, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_dev, n_max,
+                                                   shift, nb, c->hist);
+        cur ^= 1;
+    }
+    *out_buf = cur;
+    return cudaGetLastError();
+}
+
+cudaError_t scan_tiles(gs_ctx* c, uint32_t n, cudaStream_t s) {
+    // the depth-sorted order is in dval[0] after the even number (4) of depth passes
+    const int G = c->sort_blocks;
+    c->launches += 3;
+    k_tile_block_sums<<<G, 256, 0, s>>>(c->dval[0], c->tiles_touched, n, c->hist);
+    k_scan_counts<<<1, 1024, 0, s>>>(c->hist, (uint32_t)G, c->dcount);
+    k_tile_scan<<<G, 256, 0, s>>>(c->dval[0], c->tiles_touched, n, c->hist, c->offsets);
+    return cudaGetLastError();
+}
+
+cudaError_t scan_u32(gs_ctx* c, const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* total_dev,
+                     cudaStream_t s) {
+    const int G = c->sort_blocks;
+    c->launches += 3;
+    k_tile_block_sums<<<G, 256, 0, s>>>(nullptr, in, n, c->hist);
+    k_scan_counts<<<1, 1024, 0, s>>>(c->hist, (uint32_t)G, total_dev);
+    k_tile_scan<<<G, 256, 0, s>>>(nullptr, in, n, c->hist, out);
+    return cudaGetLastError();
+}
+
+cudaError_t emit_pairs(gs_ctx* c, uint32_t n_items, cudaStream_t s) {
+    if (n_items == 0) return cudaSuccess;
+    ++c->launches;
+    k_emit<<<(n_items + 255) / 256, 256, 0, s>>>(c->dval[0], c->tiles_touched, c->offsets, c->rec, c->dcam, c->n,
+                                                 c->tile, n_items, (uint64_t)c->pair_cap, c->pkey[0], c->pval[0],
+                                                 c->dcount + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t compute_ranges(gs_ctx* c, cudaStream_t s) {
+    cudaMemsetAsync(c->ranges, 0, sizeof(uint2) * (size_t)c->n_bins, s);
+    ++c->launches;
+    k_ranges<<<c->num_sms * 8, 256, 0, s>>>(c->pkey[c->pair_buf], c->dcount, (uint64_t)c->pair_cap,
+                                            (uint32_t)c->n_bins, c->ranges);
+    return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,268 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Small single-view workload: 2,000 frustum Gaussians, 160x120, fx = fy = 150
+(10 x 8 tiles of 16 px with a ragged last tile row). Bins and sort order are
+compared bit-exactly (the oracle's binning is fed the kernel's FP32 screen
+quantities); images within 1e-4 absolute away from pixels where a discrete
+decision lies within FP32 rounding of its threshold; gradients within 1e-3
+relative (floored at 1e-4 of the group's largest gradient).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from synth import Camera, frustum_scene, random_target
+
+from gpu_helpers import (GRAD_RTOL, IMG_ATOL, cuda, grad_errors, new_map, oracle_project_np, rotated_cam)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def scene():
+    p, cam = frustum_scene()
+    tg = random_target(160, 120, seed=1)
+    return p, cam, tg
+
+
+@pytest.fixture(scope="module")
+def ref(scene):
+    p, cam, tg = scene
+    p64 = p.astype(np.float64)
+    fwd = O.render(p64, cam, flags=True)
+    g = O.loss_and_grads(p64, [cam], tg, want_2d=True, flags=True)
+    return fwd, g
+
+
+@pytest.fixture(scope="module")
+def gpu_run(scene):
+    p, cam, tg = scene
+    gm = new_map(p.shape[1])
+    gm.set_params(cuda(p))
+    rgb, T, am = gm.render(cam, want_T=True, want_argmax=True)
+    loss = gm.loss(cuda(tg))
+    gm.backward()
+    torch.cuda.synchronize()
+    out = dict(rgb=rgb[0].cpu().numpy(), T=T[0].cpu().numpy(), argmax=am[0].cpu().numpy(),
+               loss=loss.cpu().numpy(), grads=gm.grads().cpu().numpy(), grad2d=gm.debug_grad2d()[0],
+               proj=gm.debug_projection(0), pairs=gm.debug_pairs(), tile=gm.tile_size)
+    out["map"] = gm
+    return out
+
+
+def test_projection_matches_oracle(scene, gpu_run):
+    p, cam, _ = scene
+    pr = oracle_project_np(p.astype(np.float64), cam)
+    g = gpu_run["proj"]
+    valid = g[8] > 0
+    assert np.array_equal(valid, pr["valid"])
+    v = valid
+    # screen mean in float64, stored as integer + float32 fraction: error < 1e-6 px
+    np.testing.assert_allclose(g[0][v], pr["u"][v], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(g[1][v], pr["v"][v], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(g[5][v], pr["depth"][v], rtol=1e-7)
+    for k, name in ((2, "a"), (3, "b"), (4, "c")):
+        scale = np.maximum(np.abs(pr["a"][v]), np.abs(pr["c"][v]))
+        assert np.max(np.abs(g[k][v] - pr[name][v]) / scale) < 1e-4, name
+    # integer radius equal except where 3 sqrt(lambda) sits within rounding of an integer
+    s3 = 3 * np.sqrt(pr["lam"])
+    amb = np.abs(s3 - np.round(s3)) < 1e-4 * s3
+    assert np.array_equal(g[6][v & ~amb], pr["r"][v & ~amb])
+
+
+def test_pairs_bit_exact(scene, gpu_run):
+    """Tile lists and their (tile, depth, id) order equal the oracle's definition bit for bit."""
+    p, cam, _ = scene
+    g = gpu_run["proj"]
+    bins, vals = gpu_run["pairs"]
+    depth32 = g[5].astype(np.float32)
+    keys_gpu = (bins.astype(np.uint64) << np.uint64(32)) | depth32[vals].view(np.uint32).astype(np.uint64)
+    keys_ref, vals_ref = O.bin_pairs(g[0], g[1], g[6], depth32, g[8] > 0, cam.width, cam.height, gpu_run["tile"])
+    assert keys_gpu.shape == keys_ref.shape
+    np.testing.assert_array_equal(keys_gpu, keys_ref)
+    np.testing.assert_array_equal(vals, vals_ref)
+    counts = O.tiles_touched(g[0], g[1], g[6], g[8] > 0, cam.width, cam.height, gpu_run["tile"])
+    np.testing.assert_array_equal(g[7].astype(np.int64), counts)
+
+
+def test_image_matches_oracle(ref, gpu_run):
+    fwd, _ = ref
+    near = fwd["near"]
+    assert near.mean() < 1e-3, near.sum()
+    err = np.abs(gpu_run["rgb"] - fwd["rgb"]).max(axis=0)
+    assert err[~near].max() <= IMG_ATOL, err[~near].max()
+    errT = np.abs(gpu_run["T"] - fwd["T"])
+    assert errT[~near].max() <= IMG_ATOL, errT[~near].max()
+
+
+def test_argmax_matches_oracle(ref, gpu_run):
+    """Eq. 8 argmax id: equal wherever the two largest weights are not within FP32 rounding."""
+    fwd, _ = ref
+    ok = ~fwd["near"] & (fwd["argmax_gap"] > 1e-4)
+    np.testing.assert_array_equal(gpu_run["argmax"][ok], fwd["argmax"][ok])
+
+
+def test_loss_matches_oracle(ref, gpu_run):
+    _, g = ref
+    L = gpu_run["loss"]
+    assert abs(L[0] - g["loss"]) <= 1e-5 * g["loss"]
+    assert abs(L[2] - g["reg"]) <= 1e-5 * g["reg"]
+
+
+def test_screen_gradients_match_oracle(ref, gpu_run):
+    _, g = ref
+    g2 = g["grad2d"][0]
+    gpu = gpu_run["grad2d"]
+    keep = ~g["gauss_near"]
+    names = ["u", "v", "a", "b", "c", "o"]
+    for k, name in enumerate(names):
+        ref_k = g2[name]
+        floor = 1e-4 * np.abs(ref_k).max()
+        rel = np.abs(gpu[k] - ref_k)[keep] / np.maximum(np.abs(ref_k[keep]), floor)
+        assert rel.max() <= GRAD_RTOL, (name, rel.max())
+    for c in range(3):
+        ref_k = g2["rgb"][:, c]
+        floor = 1e-4 * np.abs(ref_k).max()
+        rel = np.abs(gpu[6 + c] - ref_k)[keep] / np.maximum(np.abs(ref_k[keep]), floor)
+        assert rel.max() <= GRAD_RTOL, ("rgb", c, rel.max())
+
+
+def test_parameter_gradients_match_oracle(ref, gpu_run):
+    _, g = ref
+    errs = grad_errors(gpu_run["grads"], g["grad"], exclude=g["gauss_near"])
+    assert max(errs.values()) <= GRAD_RTOL, errs
+    assert g["gauss_near"].mean() < 0.01
+
+
+def test_adam_step_matches_oracle(scene, gpu_run):
+    """One Adam step of the kernel equals the oracle's update applied to the kernel's gradient."""
+    p, cam, tg = scene
+    gm = new_map(p.shape[1])
+    gm.set_params(cuda(p))
+    gm.render(cam)
+    gm.loss(cuda(tg))
+    gm.backward()
+    g = gm.grads().cpu().numpy().astype(np.float64)
+    gm.step()
+    after = gm.params().cpu().numpy()
+    expect, _, _ = O.adam_step(p.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1)
+    np.testing.assert_allclose(after, expect, rtol=1e-6, atol=1e-7)
+
+
+def test_tile_size_invariance(scene):
+    """Pixel-exact membership makes the image independent of the tile size, bit for bit."""
+    p, cam, _ = scene
+    outs = []
+    for tile in (8, 16):
+        gm = new_map(p.shape[1], tile_size=tile)
+        gm.set_params(cuda(p))
+        rgb, T = gm.render(cam, want_T=True)
+        assert gm.tile_size == tile
+        outs.append((rgb.cpu().numpy(), T.cpu().numpy()))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+
+
+def test_window_of_three_views(scene):
+    """Three views in one call: images per view and the summed gradient match the oracle."""
+    p, cam, _ = scene
+    cams = [cam, rotated_cam(cam, [0.03, -0.05, 0.01], [0.05, 0.0, 0.1]),
+            rotated_cam(cam, [-0.02, 0.06, 0.0], [-0.08, 0.02, -0.05])]
+    tg = random_target(160, 120, seed=5, n_views=3)
+    p64 = p.astype(np.float64)
+    g = O.loss_and_grads(p64, cams, tg, flags=True)
+    gm = new_map(p.shape[1], views=3)
+    gm.set_params(cuda(p))
+    rgb = gm.render(cams).cpu().numpy()
+    L = gm.loss(cuda(tg)).cpu().numpy()
+    gm.backward()
+    grads = gm.grads().cpu().numpy()
+    for v in range(3):
+        near = O.render(p64, cams[v], flags=True)["near"]
+        err = np.abs(rgb[v] - g["images"][v]).max(axis=0)
+        assert err[~near].max() <= IMG_ATOL
+    assert abs(L[0] - g["loss"]) <= 1e-5 * g["loss"]
+    errs = grad_errors(grads, g["grad"], exclude=g["gauss_near"])
+    assert max(errs.values()) <= GRAD_RTOL, errs
+
+
+def test_empty_map_and_all_culled():
+    cam = Camera(40, 30, 50.0, 50.0, 20.0, 15.0)
+    gm = new_map(16, W=40, H=30)
+    rgb, T = gm.render(cam, want_T=True)
+    assert float(rgb.abs().max()) == 0.0 and float(T.min()) == 1.0
+    p = np.zeros((14, 4), np.float32)
+    p[2] = -1.0                      # all behind the camera
+    p[3:6] = -2.0
+    p[6] = 1.0
+    gm.set_params(cuda(p))
+    rgb, T = gm.render(cam, want_T=True)
+    assert float(rgb.abs().max()) == 0.0 and float(T.min()) == 1.0
+    gm.loss(cuda(np.full((1, 3, 30, 40), 0.5, np.float32)))
+    gm.backward()
+    g = gm.grads().cpu().numpy()
+    # only the planar term: d/dlog-scale on the first smallest axis = s / N
+    assert np.all(g[[0, 1, 2, 6, 7, 8, 9, 10, 11, 12, 13]] == 0)
+    np.testing.assert_allclose(g[3], np.exp(-2.0) / 4, rtol=1e-6)
+    assert np.all(g[4:6] == 0)
+    bins, vals = gm.debug_pairs()
+    assert bins.size == 0
+
+
+def test_single_gaussian_closed_form():
+    """Isotropic on-axis Gaussian: the kernel's footprint matches o exp(-d^2 / (2 sigma2))."""
+    f, z, s, o = 100.0, 2.0, 0.05, 0.5
+    cam = Camera(64, 64, f, f, 32.0, 32.0)
+    p = np.zeros((14, 1), np.float32)
+    p[2] = z
+    p[3:6] = np.log(s)
+    p[6] = 1.0
+    p[10] = 0.0
+    p[11:14, 0] = [0.2, 0.6, 1.0]
+    gm = new_map(1, W=64, H=64)
+    gm.set_params(cuda(p))
+    rgb = gm.render(cam).cpu().numpy()[0]
+    sig2 = (f * s / z) ** 2 + 0.3
+    yy, xx = np.mgrid[0:64, 0:64]
+    d2 = (xx - 32.0) ** 2 + (yy - 32.0) ** 2
+    a = o * np.exp(-d2 / (2 * sig2))
+    a[(np.maximum(np.abs(xx - 32), np.abs(yy - 32)) > 8) | (a < 1 / 255)] = 0
+    np.testing.assert_allclose(rgb, np.array([0.2, 0.6, 1.0])[:, None, None] * a[None], atol=2e-7)
+
+
+def test_ragged_sizes_and_many_tiles():
+    """Image sizes that are no multiple of the tile, with Gaussians of every size."""
+    p, cam = frustum_scene(n=700, width=77, height=45, fx=70, fy=70, cx=38.5, cy=22.5, seed=9,
+                           logscale_mean=-2.5, logscale_std=1.0)
+    p64 = p.astype(np.float64)
+    fwd = O.render(p64, cam, flags=True)
+    for tile in (8, 16):
+        gm = new_map(700, W=77, H=45, tile_size=tile)
+        gm.set_params(cuda(p))
+        rgb = gm.render(cam).cpu().numpy()[0]
+        err = np.abs(rgb - fwd["rgb"]).max(axis=0)
+        assert err[~fwd["near"]].max() <= IMG_ATOL
+
+
+def test_rasterize_autograd_function(scene):
+    """torch.autograd path: gradient of an arbitrary upstream loss equals the oracle's chain."""
+    from paper_2504_02437_gb300.api import rasterize
+    p, cam, tg = scene
+    gm = new_map(p.shape[1])
+    params = cuda(p).requires_grad_(True)
+    img = rasterize(params, gm, cam)
+    w = torch.linspace(-1, 1, img.numel(), device="cuda").reshape(img.shape)
+    (img * w).sum().backward()
+    g_gpu = params.grad.cpu().numpy()
+    # oracle: the same upstream gradient w through the 2D quantities
+    p64 = torch.tensor(p, dtype=torch.float64, requires_grad=True)
+    pr = O.project(p64, cam)
+    py, px = np.meshgrid(np.arange(120), np.arange(160), indexing="ij")
+    res = O.composite(px.ravel(), py.ravel(), pr, O.Config(), flags=True)
+    wt = torch.tensor(w.cpu().numpy()[0].reshape(3, -1).T, dtype=torch.float64)
+    (res["rgb"] * wt).sum().backward()
+    near = np.zeros(p.shape[1], bool)
+    near[res["cols"][res["pair_near_grad"].any(0)].numpy()] = True
+    errs = grad_errors(g_gpu, p64.grad.numpy(), exclude=near)
+    assert max(errs.values()) <= GRAD_RTOL, errs
