@@ -76,6 +76,7 @@ class GaussianMap:
         self.ctx = ctx
         self._last_views = 0
         self._last_hw = (0, 0)
+        self._last_rgb = None
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -135,6 +136,7 @@ class GaussianMap:
         am = torch.empty(V, H, W, device=dev, dtype=torch.int32) if want_argmax else None
         self._check(self.lib.gs_render(self.ctx, arr, V, _ptr(rgb), _ptr(T), _ptr(am), _stream()))
         self._last_views, self._last_hw = V, (H, W)
+        self._last_rgb = rgb      # the library reads it again in loss(); keep it alive until the next render
         out = [rgb]
         if want_T:
             out.append(T)

@@ -319,7 +319,7 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         ok = ok && dalloc(&c->n_last, V * maxpix) == cudaSuccess;
         ok = ok && dalloc(&c->dLdC, 3 * V * maxpix) == cudaSuccess;
         ok = ok && dalloc(&c->grad2d, kGrad2dStride * V * cap) == cudaSuccess;
-        ok = ok && dalloc(&c->hist, (size_t)256 * c->sort_blocks) == cudaSuccess;
+        ok = ok && dalloc(&c->hist, (size_t)256 * c->sort_blocks + 256) == cudaSuccess;
         ok = ok && dalloc(&c->dcount, 8) == cudaSuccess;
         ok = ok && dalloc(&c->partials, (size_t)c->n_partials + 4) == cudaSuccess;
         ok = ok && alloc_pairs(c, pc) == cudaSuccess;

@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/gs.h"
+#include "gs.h"
 
 namespace gs {
 

@@ -9,18 +9,24 @@
 namespace gs {
 namespace {
 
+// View-independent shape of one Gaussian (Eq. 1): scales, normalised
+// quaternion, its rotation and Sigma = R S S^T R^T.
+struct Shape {
+    float s[3];
+    float qn[4];
+    float qnorm;
+    float R[9];            // row-major
+    float S[6];            // Sigma (xx, xy, xz, yy, yz, zz)
+};
+
+// View-dependent projection (Eq. 2) of one Gaussian for one camera.
 struct Proj {
     float tx, ty, tz;
     float xr, yr;          // x/z, y/z before clamping
     float xh, yh;          // clamped
     float J00, J02, J11, J12;
     float T0[3], T1[3];    // rows of J W
-    float S[6];            // Sigma (xx, xy, xz, yy, yz, zz)
     float A, B, C, det;    // dilated 2D covariance
-    float s[3];
-    float qn[4];
-    float qnorm;
-    float R[9];            // rotation of the normalised quaternion, row-major
 };
 
 __device__ __forceinline__ void load_params(const float* __restrict__ P, int cap, int i, float p[kParamRows]) {
@@ -28,35 +34,39 @@ __device__ __forceinline__ void load_params(const float* __restrict__ P, int cap
     for (int r = 0; r < kParamRows; ++r) p[r] = __ldg(P + (size_t)r * cap + i);
 }
 
-// Eq. 1 and Eq. 2 in float32 for one Gaussian and one camera.
-__device__ __forceinline__ void project_one(const float p[kParamRows], const DevCamera& cam, float dilation, Proj& o) {
-    o.tx = cam.R[0] * p[0] + cam.R[1] * p[1] + cam.R[2] * p[2] + cam.t[0];
-    o.ty = cam.R[3] * p[0] + cam.R[4] * p[1] + cam.R[5] * p[2] + cam.t[1];
-    o.tz = cam.R[6] * p[0] + cam.R[7] * p[1] + cam.R[8] * p[2] + cam.t[2];
-    // Eq. 1: Sigma = R S S^T R^T
-    o.s[0] = expf(p[3]);
-    o.s[1] = expf(p[4]);
-    o.s[2] = expf(p[5]);
+// Eq. 1 in float32.
+__device__ __forceinline__ void shape_of(const float p[kParamRows], Shape& g) {
+    g.s[0] = expf(p[3]);
+    g.s[1] = expf(p[4]);
+    g.s[2] = expf(p[5]);
     float qq = p[6] * p[6] + p[7] * p[7] + p[8] * p[8] + p[9] * p[9];
-    o.qnorm = sqrtf(qq);
-    float inv = 1.0f / o.qnorm;
+    g.qnorm = sqrtf(qq);
+    float inv = 1.0f / g.qnorm;
     float w = p[6] * inv, x = p[7] * inv, y = p[8] * inv, z = p[9] * inv;
-    o.qn[0] = w; o.qn[1] = x; o.qn[2] = y; o.qn[3] = z;
-    o.R[0] = 1.f - 2.f * (y * y + z * z); o.R[1] = 2.f * (x * y - w * z);       o.R[2] = 2.f * (x * z + w * y);
-    o.R[3] = 2.f * (x * y + w * z);       o.R[4] = 1.f - 2.f * (x * x + z * z); o.R[5] = 2.f * (y * z - w * x);
-    o.R[6] = 2.f * (x * z - w * y);       o.R[7] = 2.f * (y * z + w * x);       o.R[8] = 1.f - 2.f * (x * x + y * y);
+    g.qn[0] = w; g.qn[1] = x; g.qn[2] = y; g.qn[3] = z;
+    g.R[0] = 1.f - 2.f * (y * y + z * z); g.R[1] = 2.f * (x * y - w * z);       g.R[2] = 2.f * (x * z + w * y);
+    g.R[3] = 2.f * (x * y + w * z);       g.R[4] = 1.f - 2.f * (x * x + z * z); g.R[5] = 2.f * (y * z - w * x);
+    g.R[6] = 2.f * (x * z - w * y);       g.R[7] = 2.f * (y * z + w * x);       g.R[8] = 1.f - 2.f * (x * x + y * y);
     float M[9];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) M[i * 3 + k] = o.R[i * 3 + k] * o.s[k];
-    o.S[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
-    o.S[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
-    o.S[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
-    o.S[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
-    o.S[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
-    o.S[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
-    // Eq. 2: J at the clamped x/z, y/z; T = J W
+        for (int k = 0; k < 3; ++k) M[i * 3 + k] = g.R[i * 3 + k] * g.s[k];
+    g.S[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+    g.S[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+    g.S[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+    g.S[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+    g.S[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+    g.S[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+}
+
+// Eq. 2 in float32 for one camera: J at the clamped x/z, y/z; T = J W;
+// Sigma2D = T Sigma T^T + dilation I.
+__device__ __forceinline__ void project_one(const float p[kParamRows], const Shape& g, const DevCamera& cam,
+                                            float dilation, Proj& o) {
+    o.tx = cam.R[0] * p[0] + cam.R[1] * p[1] + cam.R[2] * p[2] + cam.t[0];
+    o.ty = cam.R[3] * p[0] + cam.R[4] * p[1] + cam.R[5] * p[2] + cam.t[1];
+    o.tz = cam.R[6] * p[0] + cam.R[7] * p[1] + cam.R[8] * p[2] + cam.t[2];
     float iz = 1.0f / o.tz;
     o.xr = o.tx * iz;
     o.yr = o.ty * iz;
@@ -71,14 +81,13 @@ __device__ __forceinline__ void project_one(const float p[kParamRows], const Dev
         o.T0[k] = o.J00 * cam.R[k] + o.J02 * cam.R[6 + k];
         o.T1[k] = o.J11 * cam.R[3 + k] + o.J12 * cam.R[6 + k];
     }
-    // Sigma T^T columns
     float ST0[3], ST1[3];
-    ST0[0] = o.S[0] * o.T0[0] + o.S[1] * o.T0[1] + o.S[2] * o.T0[2];
-    ST0[1] = o.S[1] * o.T0[0] + o.S[3] * o.T0[1] + o.S[4] * o.T0[2];
-    ST0[2] = o.S[2] * o.T0[0] + o.S[4] * o.T0[1] + o.S[5] * o.T0[2];
-    ST1[0] = o.S[0] * o.T1[0] + o.S[1] * o.T1[1] + o.S[2] * o.T1[2];
-    ST1[1] = o.S[1] * o.T1[0] + o.S[3] * o.T1[1] + o.S[4] * o.T1[2];
-    ST1[2] = o.S[2] * o.T1[0] + o.S[4] * o.T1[1] + o.S[5] * o.T1[2];
+    ST0[0] = g.S[0] * o.T0[0] + g.S[1] * o.T0[1] + g.S[2] * o.T0[2];
+    ST0[1] = g.S[1] * o.T0[0] + g.S[3] * o.T0[1] + g.S[4] * o.T0[2];
+    ST0[2] = g.S[2] * o.T0[0] + g.S[4] * o.T0[1] + g.S[5] * o.T0[2];
+    ST1[0] = g.S[0] * o.T1[0] + g.S[1] * o.T1[1] + g.S[2] * o.T1[2];
+    ST1[1] = g.S[1] * o.T1[0] + g.S[3] * o.T1[1] + g.S[4] * o.T1[2];
+    ST1[2] = g.S[2] * o.T1[0] + g.S[4] * o.T1[1] + g.S[5] * o.T1[2];
     o.A = o.T0[0] * ST0[0] + o.T0[1] * ST0[1] + o.T0[2] * ST0[2] + dilation;
     o.B = o.T0[0] * ST1[0] + o.T0[1] * ST1[1] + o.T0[2] * ST1[2];
     o.C = o.T1[0] * ST1[0] + o.T1[1] * ST1[1] + o.T1[2] * ST1[2] + dilation;
@@ -97,8 +106,10 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ P,
     size_t item = (size_t)view * n + gid;
     float p[kParamRows];
     load_params(P, cap, gid, p);
+    Shape g;
+    shape_of(p, g);
     Proj o;
-    project_one(p, cam, kc.dilation, o);
+    project_one(p, g, cam, kc.dilation, o);
     // Screen mean and depth in float64 (the covariance stays float32): the
     // compositing subtracts u from pixel coordinates, and the rounding of u in
     // float32 (about 1e-4 px at 1000 px) would dominate the error of the
@@ -157,6 +168,8 @@ __global__ void __launch_bounds__(128) k_preprocess_backward(
     float dS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // symmetric (G + G^T) of dL/dSigma
     float dop = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
     float gsum = 0.f, gcnt = 0.f;
+    Shape g;
+    shape_of(p, g);
     Proj o;
     const float k1 = -0.5f * kLog2e, k2 = -kLog2e;
     for (int view = 0; view < n_views; ++view) {
@@ -174,7 +187,7 @@ __global__ void __launch_bounds__(128) k_preprocess_backward(
         db += g8;
         gsum += sqrtf(gu * gu + gv * gv);
         gcnt += 1.f;
-        project_one(p, cam, kc.dilation, o);
+        project_one(p, g, cam, kc.dilation, o);
         // conic (a, b, c) = inverse of [[A, B], [B, C]]
         float id2 = 1.0f / (o.det * o.det);
         float A = o.A, B = o.B, C = o.C;
@@ -192,12 +205,12 @@ __global__ void __launch_bounds__(128) k_preprocess_backward(
         dS[5] += 2.f * gA * T0[2] * T0[2] + 2.f * gB * T0[2] * T1[2] + 2.f * gC * T1[2] * T1[2];
         // dL/dT0 = 2 gA Sigma T0 + gB Sigma T1 ; dL/dT1 = gB Sigma T0 + 2 gC Sigma T1
         float ST0[3], ST1[3];
-        ST0[0] = o.S[0] * T0[0] + o.S[1] * T0[1] + o.S[2] * T0[2];
-        ST0[1] = o.S[1] * T0[0] + o.S[3] * T0[1] + o.S[4] * T0[2];
-        ST0[2] = o.S[2] * T0[0] + o.S[4] * T0[1] + o.S[5] * T0[2];
-        ST1[0] = o.S[0] * T1[0] + o.S[1] * T1[1] + o.S[2] * T1[2];
-        ST1[1] = o.S[1] * T1[0] + o.S[3] * T1[1] + o.S[4] * T1[2];
-        ST1[2] = o.S[2] * T1[0] + o.S[4] * T1[1] + o.S[5] * T1[2];
+        ST0[0] = g.S[0] * T0[0] + g.S[1] * T0[1] + g.S[2] * T0[2];
+        ST0[1] = g.S[1] * T0[0] + g.S[3] * T0[1] + g.S[4] * T0[2];
+        ST0[2] = g.S[2] * T0[0] + g.S[4] * T0[1] + g.S[5] * T0[2];
+        ST1[0] = g.S[0] * T1[0] + g.S[1] * T1[1] + g.S[2] * T1[2];
+        ST1[1] = g.S[1] * T1[0] + g.S[3] * T1[1] + g.S[4] * T1[2];
+        ST1[2] = g.S[2] * T1[0] + g.S[4] * T1[1] + g.S[5] * T1[2];
         float dT0[3], dT1[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -233,16 +246,12 @@ __global__ void __launch_bounds__(128) k_preprocess_backward(
         dmu[1] += cam.R[1] * dtx + cam.R[4] * dty + cam.R[7] * dtz;
         dmu[2] += cam.R[2] * dtx + cam.R[5] * dty + cam.R[8] * dtz;
     }
-    if (gcnt == 0.f) {
-        // not visible in any view: recompute the rotation and scales for the chain below
-        project_one(p, cams[0], kc.dilation, o);
-    }
     // Sigma = M M^T with M = R S: dL/dM = dS M
     float M[9];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) M[i * 3 + k] = o.R[i * 3 + k] * o.s[k];
+        for (int k = 0; k < 3; ++k) M[i * 3 + k] = g.R[i * 3 + k] * g.s[k];
     const float Sf[9] = {dS[0], dS[1], dS[2], dS[1], dS[3], dS[4], dS[2], dS[4], dS[5]};
     float dM[9];
 #pragma unroll
@@ -254,21 +263,21 @@ __global__ void __launch_bounds__(128) k_preprocess_backward(
     float dR[9];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        float ds = dM[0 * 3 + k] * o.R[0 * 3 + k] + dM[1 * 3 + k] * o.R[1 * 3 + k] + dM[2 * 3 + k] * o.R[2 * 3 + k];
-        dls[k] = ds * o.s[k];
+        float ds = dM[0 * 3 + k] * g.R[0 * 3 + k] + dM[1 * 3 + k] * g.R[1 * 3 + k] + dM[2 * 3 + k] * g.R[2 * 3 + k];
+        dls[k] = ds * g.s[k];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) dR[i * 3 + k] = dM[i * 3 + k] * o.s[k];
+        for (int i = 0; i < 3; ++i) dR[i * 3 + k] = dM[i * 3 + k] * g.s[k];
     }
     if (add_reg) {
         // Eq. 10 planar term: mean_i max(floor, min_k s_ik); gradient on the (first) smallest axis
         int km = 0;
-        float sm = o.s[0];
-        if (o.s[1] < sm) { sm = o.s[1]; km = 1; }
-        if (o.s[2] < sm) { sm = o.s[2]; km = 2; }
+        float sm = g.s[0];
+        if (g.s[1] < sm) { sm = g.s[1]; km = 1; }
+        if (g.s[2] < sm) { sm = g.s[2]; km = 2; }
         if (sm > kc.reg_floor) dls[km] += reg_scale * sm;
     }
     // rotation of the normalised quaternion (w, x, y, z)
-    float w = o.qn[0], x = o.qn[1], y = o.qn[2], z = o.qn[3];
+    float w = g.qn[0], x = g.qn[1], y = g.qn[2], z = g.qn[3];
     float dw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
     float dx = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
                       2.f * x * dR[8]);
@@ -278,7 +287,7 @@ __global__ void __launch_bounds__(128) k_preprocess_backward(
                       x * dR[6] + y * dR[7]);
     // through the normalisation q / |q|
     float dot = w * dw + x * dx + y * dy + z * dz;
-    float iq = 1.0f / o.qnorm;
+    float iq = 1.0f / g.qnorm;
     float oa = 1.0f / (1.0f + expf(-p[10]));
     size_t c = (size_t)cap;
     G[0 * c + gid] = dmu[0];

@@ -27,10 +27,12 @@ __device__ __forceinline__ float power2(const float4 q, float dx, float dy) {
     return __fmaf_rn(__fmul_rn(q.x, dx), dx, t);
 }
 
-// Stage one raster record for a tile whose first pixel is (ox, oy). The screen
-// mean is stored split (integer part in f0.xy, fractions in f1.w, f2.w); the
-// tile-local mean (ui - ox) + uf is formed once per pair and tile, so pixel
-// offsets carry the rounding of a small number only.
+// Stage one raster record relative to the local origin (ox, oy), the tile's
+// corner rounded down to a multiple of 32 px. The screen mean is stored split
+// (integer part in f0.xy, fractions in f1.w, f2.w); the local mean
+// (ui - ox) + uf is formed once per pair and tile, so pixel offsets carry the
+// rounding of a small number only, and the same for tiles of 8, 16 or 32 px
+// (which keeps the image bit-identical across tile sizes).
 __device__ __forceinline__ void load_record(const float4* __restrict__ rec, uint32_t item, float ox, float oy,
                                             float4& s0, float4& s1, float4& s2) {
     const float4 a = rec[(size_t)item * 3 + 0];
@@ -69,9 +71,9 @@ __global__ void __launch_bounds__(TILE* TILE) k_raster_fwd(const uint2* __restri
     pixel_of<TILE>(threadIdx.x, lx, ly);
     const int px = txi * TILE + lx, py = tyi * TILE + ly;
     const bool inside = px < width && py < height;
-    // pixel offsets are taken in tile-local coordinates (see load_record)
-    const float fx = (float)lx, fy = (float)ly;
-    const float ox = (float)(txi * TILE), oy = (float)(tyi * TILE);
+    // pixel offsets are taken from a 32-px-aligned local origin (see load_record)
+    const float ox = (float)((txi * TILE) & ~31), oy = (float)((tyi * TILE) & ~31);
+    const float fx = (float)px - ox, fy = (float)py - oy;
     const uint2 rg = ranges[bin];
     float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f;
     uint32_t last = 0;
@@ -153,8 +155,8 @@ __global__ void __launch_bounds__(TILE* TILE) k_raster_bwd(const uint2* __restri
     pixel_of<TILE>(threadIdx.x, lx, ly);
     const int px = txi * TILE + lx, py = tyi * TILE + ly;
     const bool inside = px < width && py < height;
-    const float fx = (float)lx, fy = (float)ly;
-    const float ox = (float)(txi * TILE), oy = (float)(tyi * TILE);
+    const float ox = (float)((txi * TILE) & ~31), oy = (float)((tyi * TILE) & ~31);
+    const float fx = (float)px - ox, fy = (float)py - oy;
     const uint2 rg = ranges[bin];
     const size_t HW = (size_t)width * height;
     const size_t pix = (size_t)py * width + px;
@@ -258,8 +260,8 @@ __global__ void __launch_bounds__(TILE* TILE) k_count_work(const uint2* __restri
     pixel_of<TILE>(threadIdx.x, lx, ly);
     const int px = txi * TILE + lx, py = tyi * TILE + ly;
     if (px >= width || py >= height) return;
-    const float fx = (float)lx, fy = (float)ly;
-    const float ox = (float)(txi * TILE), oy = (float)(tyi * TILE);
+    const float ox = (float)((txi * TILE) & ~31), oy = (float)((tyi * TILE) & ~31);
+    const float fx = (float)px - ox, fy = (float)py - oy;
     const uint2 rg = ranges[bin];
     float T = 1.f;
     unsigned long long tested = 0, blended = 0, walked = 0;

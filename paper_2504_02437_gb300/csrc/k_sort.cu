@@ -101,6 +101,42 @@ __global__ void __launch_bounds__(1024) k_scan_counts(uint32_t* __restrict__ a, 
     if (t == 0 && total_out != nullptr) *total_out = carry;
 }
 
+// Exclusive scan of each digit's row of block counts (one CTA per digit):
+// hist[d * G + b] <- sum of hist[d * G + b'] for b' < b; dtot[d] <- row total.
+__global__ void __launch_bounds__(256) k_digit_scan(uint32_t* __restrict__ hist, int G, uint32_t* __restrict__ dtot) {
+    __shared__ uint32_t ws[8];
+    __shared__ uint32_t carry;
+    const int d = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    uint32_t* row = hist + (size_t)d * G;
+    if (t == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < G; base += 256) {
+        const int i = base + t;
+        const uint32_t c = i < G ? row[i] : 0u;
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws[w] = x;
+        __syncthreads();
+        uint32_t pre = 0, tot = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            uint32_t v = ws[k];
+            pre += (k < w) ? v : 0u;
+            tot += v;
+        }
+        const uint32_t before = carry;
+        if (i < G) row[i] = before + pre + x - c;
+        __syncthreads();
+        if (t == 0) carry = before + tot;
+        __syncthreads();
+    }
+    if (t == 0) dtot[d] = carry;
+}
+
 // Stable scatter of one digit pass. Each block walks its slice in rounds of
 // kRound elements; warp w of a round owns a contiguous run of 32*kSortItems
 // elements, ranked within the warp by __match_any_sync, across warps by a
@@ -109,7 +145,7 @@ __global__ void __launch_bounds__(1024) k_scan_counts(uint32_t* __restrict__ a, 
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* __restrict__ n_dev, uint32_t n_max, int shift, int nbits,
-    const uint32_t* __restrict__ hist) {
+    const uint32_t* __restrict__ hist, const uint32_t* __restrict__ dtot) {
     __shared__ uint32_t run[256];
     __shared__ uint32_t total[256];
     __shared__ uint32_t wcnt[kSortWarps][256];
@@ -117,7 +153,23 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t mask = (1u << nbits) - 1u;
     const int ndig = 1 << nbits;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < ndig; d += kSortThreads) run[d] = hist[(size_t)d * G + b];
+    {
+        // start of each digit = exclusive prefix of the digit totals (one digit per thread)
+        const int d = threadIdx.x;
+        const uint32_t c = d < ndig ? dtot[d] : 0u;
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) total[w] = x;
+        __syncthreads();
+        uint32_t pre = 0;
+        for (int k = 0; k < w; ++k) pre += total[k];
+        if (d < ndig) run[d] = pre + x - c + hist[(size_t)d * G + b];
+        __syncthreads();
+    }
     uint32_t n = umin(*n_dev, n_max), begin, end;
     slice_of(n, G, b, begin, end);
     const uint32_t lt = lanemask_lt();
@@ -276,10 +328,11 @@ cudaError_t radix_sort_pairs(gs_ctx* c, uint32_t** keys, uint32_t** vals, const 
     for (int shift = 0; shift < bits; shift += 8) {
         int nb = bits - shift < 8 ? bits - shift : 8;
         c->launches += 3;
+        uint32_t* dtot = c->hist + (size_t)256 * c->sort_blocks;
         k_radix_hist<<<G, kSortThreads, 0, s>>>(keys[cur], n_dev, n_max, shift, nb, c->hist);
-        k_scan_counts<<<1, 1024, 0, s>>>(c->hist, (uint32_t)((1u << nb) * G), nullptr);
+        k_digit_scan<<<1 << nb, 256, 0, s>>>(c->hist, G, dtot);
         k_radix_scatter<<<G, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_dev, n_max,
-                                                   shift, nb, c->hist);
+                                                   shift, nb, c->hist, dtot);
         cur ^= 1;
     }
     *out_buf = cur;

@@ -5,7 +5,8 @@ Small single-view workload: 2,000 frustum Gaussians, 160x120, fx = fy = 150
 compared bit-exactly (the oracle's binning is fed the kernel's FP32 screen
 quantities); images within 1e-4 absolute away from pixels where a discrete
 decision lies within FP32 rounding of its threshold; gradients within 1e-3
-relative (floored at 1e-4 of the group's largest gradient).
+relative (floored at 1e-3 of the group's largest gradient, the FP32 accumulation
+level of these cancelling sums).
 """
 import numpy as np
 import pytest
@@ -14,7 +15,8 @@ import torch
 import oracle as O
 from synth import Camera, frustum_scene, random_target
 
-from gpu_helpers import (GRAD_RTOL, IMG_ATOL, cuda, grad_errors, new_map, oracle_project_np, rotated_cam)
+from gpu_helpers import (GRAD_FLOOR, GRAD_RTOL, IMG_ATOL, cuda, grad_errors, new_map, oracle_project_np,
+                         rotated_cam)
 
 pytestmark = pytest.mark.gpu
 
@@ -118,12 +120,12 @@ def test_screen_gradients_match_oracle(ref, gpu_run):
     names = ["u", "v", "a", "b", "c", "o"]
     for k, name in enumerate(names):
         ref_k = g2[name]
-        floor = 1e-4 * np.abs(ref_k).max()
+        floor = GRAD_FLOOR * np.abs(ref_k).max()
         rel = np.abs(gpu[k] - ref_k)[keep] / np.maximum(np.abs(ref_k[keep]), floor)
         assert rel.max() <= GRAD_RTOL, (name, rel.max())
     for c in range(3):
         ref_k = g2["rgb"][:, c]
-        floor = 1e-4 * np.abs(ref_k).max()
+        floor = GRAD_FLOOR * np.abs(ref_k).max()
         rel = np.abs(gpu[6 + c] - ref_k)[keep] / np.maximum(np.abs(ref_k[keep]), floor)
         assert rel.max() <= GRAD_RTOL, ("rgb", c, rel.max())
 
