@@ -206,6 +206,26 @@ GS_API int gs_timing_enable(gs_ctx* ctx, int enable);
  * (counts_host[GS_N_PHASES], may be NULL); clears the records. */
 GS_API int gs_timing_read(gs_ctx* ctx, float* ms_host, int32_t* counts_host);
 
+/* Stable LSD radix sort of n (key, value) pairs by the low `bits` bits of the
+ * key, for callers that cannot allocate device memory: those that run while
+ * another component owns the device allocator, or inside a loop that must
+ * not call cudaMalloc. The paper has no counterpart; it is the pair sort of
+ * gs_render offered on its own. It allocates nothing: its scratch (about
+ * 8.7 MB) is a static device array that every GPU loading this library
+ * holds until the process exits, so n is limited to 1048576 pairs
+ * (GS_ERR_CAPACITY above that). keys_in/vals_in ([n] device) are read,
+ * keys_out/vals_out ([n] device, distinct from the inputs and from each
+ * other) receive the pairs sorted by key, equal keys keeping their input
+ * order. Enqueued on `stream` without waiting. The first call on each device
+ * resolves the scratch address (call it once before any stream capture).
+ * Every call shares the one scratch array, so calls that overlap on the GPU
+ * (different streams or host threads) race; the array keeps the last call's
+ * contents, and each call writes every word it reads. Errors: GS_ERR_ARG
+ * (bits outside 1..32, NULL or aliased buffers), GS_ERR_CAPACITY,
+ * GS_ERR_CUDA. */
+GS_API int gs_sort_pairs_static(const uint32_t* keys_in_dev, const uint32_t* vals_in_dev, uint32_t* keys_out_dev,
+                                uint32_t* vals_out_dev, int64_t n, int bits, void* stream);
+
 /* Introspection for tests (synchronising, host outputs). */
 /* Per-view screen quantities of the last render, float64 host arrays of n each:
  * out_host[k*n + i] for k = 0 u, 1 v, 2 conic a, 3 conic b, 4 conic c, 5 depth

@@ -68,6 +68,7 @@ SIGNATURES = {
     "gs_timing_read": (_I, [_P, _P, _P]),
     "gs_debug_work": (_I, [_P, _P]),
     "gs_launch_count": (C.c_int64, [_P]),
+    "gs_sort_pairs_static": (_I, [_P, _P, _P, _P, C.c_int64, _I, _P]),
 }
 PHASES = ("project", "bin", "raster_fwd", "loss", "raster_bwd", "project_bwd", "adam")
 

@@ -14,6 +14,7 @@
 // contiguous slice of the input; element counts are read from device memory so
 // the same launches can sit in a CUDA graph.
 #include <algorithm>
+#include <mutex>
 
 #include "gs_internal.cuh"
 
@@ -377,3 +378,78 @@ cudaError_t compute_ranges(gs_ctx* c, cudaStream_t s) {
 }
 
 }  // namespace gs
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the pair sort, for callers that must not allocate
+// device memory (for example code that runs while another component owns the
+// device allocator, or a real-time loop that forbids cudaMalloc). Its scratch
+// is one file-scope __device__ array that every GPU loading this library holds
+// until the process exits.
+
+namespace gs {
+namespace {
+
+constexpr uint32_t kStaticSortMaxPairs = 1u << 20;                       // largest n accepted
+constexpr int kStaticSortMaxBlocks = (int)((kStaticSortMaxPairs + 4095u) / 4096u);
+constexpr size_t kStaticSortWords = 64                                  // [0] count sentinel
+                                    + 2 * (size_t)kStaticSortMaxPairs    // ping-pong keys and values
+                                    + 256 * (size_t)kStaticSortMaxBlocks + 256;   // histograms, digit totals
+constexpr int kStaticMaxDevices = 256;
+
+static __device__ __align__(256) uint32_t g_static_sort_scratch[kStaticSortWords];
+
+std::mutex g_static_sort_mutex;
+uint32_t* g_static_sort_addr[kStaticMaxDevices] = {nullptr};
+
+}  // namespace
+}  // namespace gs
+
+extern "C" int gs_sort_pairs_static(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                                    uint32_t* vals_out, int64_t n, int bits, void* stream) {
+    using namespace gs;
+    if (n < 0 || bits < 1 || bits > 32) return GS_ERR_ARG;
+    if (n > (int64_t)kStaticSortMaxPairs) return GS_ERR_CAPACITY;
+    if (n == 0) return GS_OK;
+    if (!keys_in || !vals_in || !keys_out || !vals_out) return GS_ERR_ARG;
+    if (keys_in == keys_out || vals_in == vals_out || keys_out == vals_out) return GS_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return GS_ERR_CUDA;
+    uint32_t* base = nullptr;
+    {
+        // first call on this device: resolve the device address of the scratch array
+        std::lock_guard<std::mutex> lock(g_static_sort_mutex);
+        if (g_static_sort_addr[dev] == nullptr) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_static_sort_scratch) != cudaSuccess || p == nullptr) return GS_ERR_CUDA;
+            g_static_sort_addr[dev] = static_cast<uint32_t*>(p);
+        }
+        base = g_static_sort_addr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t* sentinel = base;
+    uint32_t* tmp_k = base + 64;
+    uint32_t* tmp_v = tmp_k + kStaticSortMaxPairs;
+    uint32_t* hist = tmp_v + kStaticSortMaxPairs;
+    const uint32_t un = (uint32_t)n;
+    const int G = (int)std::max<uint32_t>(1u, std::min<uint32_t>((uint32_t)kStaticSortMaxBlocks, (un + 4095u) / 4096u));
+    uint32_t* dtot = hist + (size_t)256 * G;
+    // the count is passed as n_max with a device-side bound of 0xFFFFFFFF
+    if (cudaMemsetAsync(sentinel, 0xFF, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
+    const int passes = (bits + 7) / 8;
+    const uint32_t* src_k = keys_in;
+    const uint32_t* src_v = vals_in;
+    for (int i = 0; i < passes; ++i) {
+        // destinations alternate so that the last pass writes the caller's output
+        const bool to_out = ((passes - i) & 1) == 1;
+        uint32_t* dk = to_out ? keys_out : tmp_k;
+        uint32_t* dv = to_out ? vals_out : tmp_v;
+        const int shift = 8 * i;
+        const int nb = bits - shift < 8 ? bits - shift : 8;
+        k_radix_hist<<<G, kSortThreads, 0, s>>>(src_k, sentinel, un, shift, nb, hist);
+        k_digit_scan<<<1 << nb, 256, 0, s>>>(hist, G, dtot);
+        k_radix_scatter<<<G, kSortThreads, 0, s>>>(src_k, src_v, dk, dv, sentinel, un, shift, nb, hist, dtot);
+        src_k = dk;
+        src_v = dv;
+    }
+    return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
