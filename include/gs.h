@@ -84,6 +84,8 @@ typedef struct gs_config {
     float split_factor;  /* children log-scale -= ln(split_factor) (1.6)              */
     float insert_opacity;/* skip a new point if rendered opacity > this (0.99)        */
     int32_t tile_size;   /* 8 or 16 pixels; 0 = pick by the built-in autotuner        */
+    int32_t pixels_per_thread; /* compositing kernels: 1, 2 or 4 (16-px tiles), 1 or 2
+                                  (8-px tiles); 0 = the autotuner's or the default      */
     int32_t capacity;    /* maximum number of Gaussians                               */
     int32_t max_views;   /* maximum views per render call (<= GS_MAX_VIEWS)           */
     int32_t max_width, max_height; /* largest image of any view                       */
@@ -198,7 +200,8 @@ GS_API int gs_densify(gs_ctx* ctx, const float* normals_dev, int* n_split_host, 
 #define GS_PHASE_RASTER_BWD 4   /* adjoint compositing kernel                            */
 #define GS_PHASE_PROJECT_BWD 5  /* adjoint of the projection + planar gradient           */
 #define GS_PHASE_ADAM 6         /* Adam update                                           */
-#define GS_N_PHASES 7
+#define GS_PHASE_RASTER_FUSED 7 /* gs_iterate: compositing + L1 + adjoint in one kernel  */
+#define GS_N_PHASES 8
 /* enable != 0 starts recording (discarding earlier records); 0 stops. */
 GS_API int gs_timing_enable(gs_ctx* ctx, int enable);
 /* Synchronise on the recorded events and write, per phase, the summed

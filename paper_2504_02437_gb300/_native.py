@@ -36,7 +36,7 @@ class gs_config(C.Structure):
                 ("alpha_max", C.c_float), ("T_min", C.c_float), ("lambda_color", C.c_float),
                 ("lambda_reg", C.c_float), ("reg_floor", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
                 ("eps", C.c_float), ("lr", C.c_float * 5), ("split_thresh", C.c_float),
-                ("split_factor", C.c_float), ("insert_opacity", C.c_float), ("tile_size", C.c_int32),
+                ("split_factor", C.c_float), ("insert_opacity", C.c_float), ("tile_size", C.c_int32), ("pixels_per_thread", C.c_int32),
                 ("capacity", C.c_int32), ("max_views", C.c_int32), ("max_width", C.c_int32),
                 ("max_height", C.c_int32), ("pair_capacity", C.c_int64), ("seed", C.c_uint64)]
 
@@ -70,7 +70,7 @@ SIGNATURES = {
     "gs_launch_count": (C.c_int64, [_P]),
     "gs_sort_pairs_static": (_I, [_P, _P, _P, _P, C.c_int64, _I, _P]),
 }
-PHASES = ("project", "bin", "raster_fwd", "loss", "raster_bwd", "project_bwd", "adam")
+PHASES = ("project", "bin", "raster_fwd", "loss", "raster_bwd", "project_bwd", "adam", "raster_fused")
 
 _lib = None
 

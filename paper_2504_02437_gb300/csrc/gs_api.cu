@@ -12,6 +12,9 @@ using namespace gs;
 namespace {
 
 int fail(gs_ctx* c, int code, const char* what, cudaError_t e = cudaSuccess) {
+    // the error is reported here; clear the runtime's last-error slot so that a
+    // later cudaGetLastError() check does not see it again
+    if (e != cudaSuccess) cudaGetLastError();
     char buf[512];
     if (e != cudaSuccess)
         snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
@@ -36,8 +39,6 @@ __global__ void k_set_cams(CamBatch b, DevCamera* dst) {
     int i = threadIdx.x;
     if (i < b.n) dst[i] = b.cam[i];
 }
-
-__global__ void k_tick(uint32_t* t) { *t += 1u; }
 
 __global__ void k_fill(float* p, size_t n, float v) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
@@ -122,7 +123,12 @@ cudaError_t alloc_pairs(gs_ctx* c, int64_t cap) {
 
 void drop_graph(gs_ctx* c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->graph_src) cudaGraphDestroy(c->graph_src);
     c->graph = nullptr;
+    c->graph_src = nullptr;
+    c->graph_pending = false;
+    c->graph_tnodes.clear();
+    c->cam_node = nullptr;
 }
 
 int pick_tile(gs_ctx* c, int w, int h) {
@@ -136,7 +142,7 @@ int pick_tile(gs_ctx* c, int w, int h) {
 
 // Set up the per-view cameras of a render and upload them with a kernel (no
 // host-memory copy, so the same sequence can be captured into a graph).
-int setup_views(gs_ctx* c, const gs_camera* cams, int n_views, cudaStream_t s) {
+int prepare_views(gs_ctx* c, const gs_camera* cams, int n_views, CamBatch& b) {
     if (n_views < 1 || n_views > c->cfg.max_views) return fail(c, GS_ERR_ARG, "n_views out of range");
     if (cams == nullptr) return fail(c, GS_ERR_ARG, "cams is NULL");
     for (int v = 0; v < n_views; ++v) {
@@ -145,7 +151,6 @@ int setup_views(gs_ctx* c, const gs_camera* cams, int n_views, cudaStream_t s) {
             return fail(c, GS_ERR_ARG, "all views of one call must share one image size");
     }
     int tile = pick_tile(c, cams[0].width, cams[0].height);
-    CamBatch b;
     memset(&b, 0, sizeof(b));
     b.n = n_views;
     for (int v = 0; v < n_views; ++v) make_cam(cams[v], c->cfg, tile, v, b.cam[v]);
@@ -156,7 +161,16 @@ int setup_views(gs_ctx* c, const gs_camera* cams, int n_views, cudaStream_t s) {
     c->width = cams[0].width;
     c->height = cams[0].height;
     c->n_bins = bins;
+    const int want = c->cfg.pixels_per_thread;
+    c->ppt = (want == 1 || want == 2 || (want == 4 && tile == 16)) ? want : 1;
     memcpy(c->hcam, b.cam, sizeof(DevCamera) * n_views);
+    return GS_OK;
+}
+
+int setup_views(gs_ctx* c, const gs_camera* cams, int n_views, cudaStream_t s) {
+    CamBatch b;
+    int code = prepare_views(c, cams, n_views, b);
+    if (code != GS_OK) return code;
     ++c->launches;
     k_set_cams<<<1, 32, 0, s>>>(b, c->dcam);
     CK(cudaGetLastError());
@@ -187,11 +201,21 @@ struct Phase {
             end = nullptr;
             return;
         }
-        cudaEventRecord(a, s);
-        c->trec.push_back({id, a, end});
+        if (c->capturing) {
+            // captured as an event-record node; each replay is given fresh events
+            cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);
+            c->cap_phases.push_back({id, a, end});
+        } else {
+            cudaEventRecord(a, s);
+            c->trec.push_back({id, a, end});
+        }
     }
     ~Phase() {
-        if (end) cudaEventRecord(end, s);
+        if (!end) return;
+        if (c->capturing)
+            cudaEventRecordWithFlags(end, s, cudaEventRecordExternal);
+        else
+            cudaEventRecord(end, s);
     }
 };
 
@@ -206,7 +230,7 @@ int front_half(gs_ctx* c, const DevConst& k, cudaStream_t s) {
     return GS_OK;
 }
 
-// Emission, bin sort, ranges, forward raster.
+// Emission, bin sort, ranges, and (unless rgb is NULL) the forward raster.
 int back_half(gs_ctx* c, const DevConst& k, float* rgb, int32_t* argmax, cudaStream_t s) {
     const uint32_t items = (uint32_t)c->n_views * (uint32_t)c->n;
     {
@@ -218,6 +242,7 @@ int back_half(gs_ctx* c, const DevConst& k, float* rgb, int32_t* argmax, cudaStr
                             c->pairs_hint, bits, &c->pair_buf, s));
         CK(compute_ranges(c, s));
     }
+    if (!rgb) return GS_OK;
     Phase ph(c, GS_PHASE_RASTER_FWD, s);
     CK(launch_raster_forward(c, k, rgb, argmax, s));
     return GS_OK;
@@ -278,13 +303,15 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
     if (!cfg || !out) return GS_ERR_ARG;
     *out = nullptr;
     if (cfg->capacity <= 0 || cfg->max_views < 1 || cfg->max_views > GS_MAX_VIEWS || cfg->max_width <= 0 ||
-        cfg->max_height <= 0 || (cfg->tile_size != 0 && cfg->tile_size != 8 && cfg->tile_size != 16))
+        cfg->max_height <= 0 || (cfg->tile_size != 0 && cfg->tile_size != 8 && cfg->tile_size != 16) ||
+        (cfg->pixels_per_thread != 0 && cfg->pixels_per_thread != 1 && cfg->pixels_per_thread != 2 &&
+         cfg->pixels_per_thread != 4))
         return GS_ERR_ARG;
     if ((int64_t)cfg->capacity * cfg->max_views >= (int64_t)0xFFFFFFFF) return GS_ERR_ARG;
     gs_ctx* c = new gs_ctx();
     c->cfg = *cfg;
     c->device = device;
-    c->cap = cfg->capacity;
+    c->cap = (cfg->capacity + 3) & ~3;   // float4-aligned rows
     int code = GS_OK;
     do {
         cudaError_t e = cudaSetDevice(device);
@@ -321,9 +348,14 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         ok = ok && dalloc(&c->grad2d, kGrad2dStride * V * cap) == cudaSuccess;
         ok = ok && dalloc(&c->hist, (size_t)256 * c->sort_blocks + 256) == cudaSuccess;
         ok = ok && dalloc(&c->dcount, 8) == cudaSuccess;
-        ok = ok && dalloc(&c->partials, (size_t)c->n_partials + 4) == cudaSuccess;
+        ok = ok && dalloc(&c->partials, (size_t)c->n_partials + 8) == cudaSuccess;
+        c->n_fpart = 32 * c->num_sms;   // at most 32 resident CTAs per SM
+        ok = ok && dalloc(&c->fpart, (size_t)c->n_fpart) == cudaSuccess;
         ok = ok && alloc_pairs(c, pc) == cudaSuccess;
         ok = ok && cudaMallocHost((void**)&c->hcount, sizeof(uint32_t) * 8) == cudaSuccess;
+        ok = ok && cudaMallocHost((void**)&c->hflags, sizeof(uint32_t) * 4) == cudaSuccess;
+        ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&c->graph_done, cudaEventDisableTiming) == cudaSuccess;
         if (!ok) { code = fail(c, GS_ERR_OOM, "device allocation failed"); break; }
         uint32_t init[8] = {0, 0, 0, 0xFFFFFFFFu, 0, 0, 0, 0};
         e = cudaMemcpy(c->dcount, init, sizeof(init), cudaMemcpyHostToDevice);
@@ -355,10 +387,14 @@ void gs_destroy(gs_ctx* c) {
     for (auto e : c->tpool) cudaEventDestroy(e);
     void* ptrs[] = {c->params, c->grads, c->adam_m, c->adam_v, c->dens_sum, c->dens_cnt, c->dcam, c->rec,
                     c->tiles_touched, c->depth, c->dkey[0], c->dkey[1], c->dval[0], c->dval[1], c->offsets, c->ranges,
-                    c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->dcount, c->partials, c->own_rgb};
+                    c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->dcount, c->partials, c->fpart,
+                    c->own_rgb};
     for (void* p : ptrs) cudaFree(p);
     free_pairs(c);
     if (c->hcount) cudaFreeHost(c->hcount);
+    if (c->hflags) cudaFreeHost(c->hflags);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->graph_done) cudaEventDestroy(c->graph_done);
     delete c;
 }
 
@@ -487,9 +523,6 @@ int gs_step(gs_ctx* c, void* stream) {
     c->adam_t += 1;
     Phase ph(c, GS_PHASE_ADAM, s);
     CK(launch_adam(c, s));
-    ++c->launches;
-    k_tick<<<1, 1, 0, s>>>(c->dcount + 4);
-    CK(cudaGetLastError());
     c->backward_ready = false;
     return GS_OK;
 }
@@ -500,10 +533,11 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
     if (!target) return fail(c, GS_ERR_ARG, "target_dev is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(c->device));
+    if (n_views < 1 || n_views > c->cfg.max_views || !cams) return fail(c, GS_ERR_ARG, "bad views");
     if (!rgb) {
-        if (n_views < 1 || n_views > c->cfg.max_views || !cams) return fail(c, GS_ERR_ARG, "bad views");
         size_t need = (size_t)n_views * 3 * cams[0].width * cams[0].height;
         if (need > c->own_rgb_elems) {
+            drop_graph(c);
             cudaFree(c->own_rgb);
             c->own_rgb = nullptr;
             c->own_rgb_elems = 0;
@@ -512,11 +546,172 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
         }
         rgb = c->own_rgb;
     }
-    int code = gs_render(c, cams, n_views, rgb, nullptr, nullptr, stream);
+    float* loss_out = loss_dev ? loss_dev : c->partials + c->n_partials;
+    // The flags of an earlier replay: a pair-buffer overflow there skipped its Adam step.
+    if (c->graph && c->graph_pending && cudaEventQuery(c->graph_done) == cudaSuccess) {
+        c->graph_pending = false;
+        const uint32_t P = c->hflags[0];
+        if (c->hflags[1] != 0u) {
+            drop_graph(c);
+            if (alloc_pairs(c, std::min<int64_t>((int64_t)P + P / 2 + 4096, 0xFFFFFFF0ll)) != cudaSuccess)
+                return fail(c, GS_ERR_OOM, "growing the pair buffers failed");
+            return fail(c, GS_ERR_CAPACITY, "an earlier iteration overflowed the pair buffer and skipped its update; "
+                                            "the buffer has grown");
+        }
+        c->pairs_hint = P;
+    }
+    CamBatch b;
+    int code = prepare_views(c, cams, n_views, b);
     if (code != GS_OK) return code;
+    const bool same = c->graph && c->graph_views == n_views && c->graph_w == cams[0].width &&
+                      c->graph_h == cams[0].height && c->graph_n == c->n && c->graph_tile == c->tile &&
+                      c->graph_ppt == c->ppt && c->graph_pair_cap == c->pair_cap && c->graph_target == target &&
+                      c->graph_loss == loss_out && c->graph_rgb == rgb && c->graph_timing == c->timing;
+    if (same) {
+        // replay: new cameras go in as the upload kernel's parameters
+        DevCamera* dst = c->dcam;
+        void* args[2] = {&b, &dst};
+        cudaKernelNodeParams kp = {};
+        kp.func = (void*)k_set_cams;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(32);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args;
+        CK(cudaGraphExecKernelNodeSetParams(c->graph, c->cam_node, &kp));
+        if (c->timing) {
+            for (auto& tn : c->graph_tnodes) {
+                cudaEvent_t ea = take_event(c), eb = take_event(c);
+                CK(cudaGraphExecEventRecordNodeSetEvent(c->graph, tn.a, ea));
+                CK(cudaGraphExecEventRecordNodeSetEvent(c->graph, tn.b, eb));
+                c->trec.push_back({tn.phase, ea, eb});
+            }
+        }
+        CK(cudaGraphLaunch(c->graph, s));
+        CK(cudaEventRecord(c->graph_done, s));
+        c->graph_pending = true;
+        c->launches += c->graph_kernels;
+        c->adam_t += 1;
+        c->loss_ready = false;      // the fused kernel keeps dL/dC in registers
+        c->backward_ready = false;
+        c->rendered_rgb = rgb;
+        return GS_OK;
+    }
+    // First iteration of this shape: run it directly (sizing the pair buffers), then
+    // record the whole iteration into a graph for the following calls.
+    drop_graph(c);
+    if (c->n == 0) {
+        code = gs_render(c, cams, n_views, rgb, nullptr, nullptr, stream);
+        if (code == GS_OK) code = gs_loss(c, target, loss_dev, stream);
+        if (code == GS_OK) code = gs_backward(c, nullptr, stream);
+        if (code == GS_OK) code = gs_step(c, s);
+        return code;
+    }
+    if ((code = gs_render(c, cams, n_views, rgb, nullptr, nullptr, stream)) != GS_OK) return code;
     if ((code = gs_loss(c, target, loss_dev, stream)) != GS_OK) return code;
     if ((code = gs_backward(c, nullptr, stream)) != GS_OK) return code;
-    return gs_step(c, s);
+    if ((code = gs_step(c, s)) != GS_OK) return code;
+    const int64_t P = c->pairs_hint;
+    const int64_t want = std::min<int64_t>(P + P / 4 + 4096, 0xFFFFFFF0ll);
+    if (want > c->pair_cap) {
+        CK(cudaStreamSynchronize(s));
+        if (alloc_pairs(c, want) != cudaSuccess) return fail(c, GS_ERR_OOM, "growing the pair buffers failed");
+    }
+    const DevConst k = dev_const(c->cfg);
+    const int64_t launches0 = c->launches;
+    c->cap_phases.clear();
+    c->capturing = true;
+    cudaStream_t cs = c->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        c->capturing = false;
+        return fail(c, GS_ERR_CUDA, "cudaStreamBeginCapture", e);
+    }
+    int cc = GS_OK;
+    {
+        DevCamera* dst = c->dcam;
+        ++c->launches;
+        k_set_cams<<<1, 32, 0, cs>>>(b, dst);
+        cc = front_half(c, k, cs);
+        if (cc == GS_OK) cc = back_half(c, k, nullptr, nullptr, cs);
+        if (cc == GS_OK &&
+            cudaMemsetAsync(c->grad2d, 0, sizeof(float) * kGrad2dStride * c->n_views * (size_t)c->n, cs) != cudaSuccess)
+            cc = GS_ERR_CUDA;
+        int fgrid = 0;
+        if (cc == GS_OK) {
+            Phase ph(c, GS_PHASE_RASTER_FUSED, cs);
+            if (launch_raster_fused(c, k, target, rgb, c->fpart, c->n_fpart, &fgrid, cs) != cudaSuccess)
+                cc = GS_ERR_CUDA;
+        }
+        if (cc == GS_OK) {
+            Phase ph(c, GS_PHASE_LOSS, cs);
+            if (launch_loss_tail(c, k, c->fpart, fgrid, loss_out, cs) != cudaSuccess) cc = GS_ERR_CUDA;
+        }
+        if (cc == GS_OK) {
+            Phase ph(c, GS_PHASE_PROJECT_BWD, cs);
+            if (launch_preprocess_backward(c, k, true, cs) != cudaSuccess) cc = GS_ERR_CUDA;
+        }
+        if (cc == GS_OK) {
+            Phase ph(c, GS_PHASE_ADAM, cs);
+            if (launch_adam(c, cs) != cudaSuccess) cc = GS_ERR_CUDA;
+        }
+        if (cc == GS_OK &&
+            cudaMemcpyAsync(c->hflags, c->dcount, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+            cc = GS_ERR_CUDA;
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    c->capturing = false;
+    c->graph_kernels = c->launches - launches0;
+    c->launches = launches0;
+    if (cc != GS_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        return fail(c, GS_ERR_CUDA, "capturing the mapping iteration failed", e);
+    }
+    // locate the camera-upload node and the phase event nodes
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    c->graph_tnodes.clear();
+    std::vector<cudaGraphNode_t> ta(c->cap_phases.size(), nullptr), tb(c->cap_phases.size(), nullptr);
+    for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        cudaGraphNodeGetType(nd, &ty);
+        if (ty == cudaGraphNodeTypeKernel) {
+            cudaKernelNodeParams kp;
+            if (cudaGraphKernelNodeGetParams(nd, &kp) == cudaSuccess && kp.func == (void*)k_set_cams) c->cam_node = nd;
+        } else if (ty == cudaGraphNodeTypeEventRecord) {
+            cudaEvent_t ev;
+            if (cudaGraphEventRecordNodeGetEvent(nd, &ev) != cudaSuccess) continue;
+            for (size_t i = 0; i < c->cap_phases.size(); ++i) {
+                if (c->cap_phases[i].a == ev) ta[i] = nd;
+                if (c->cap_phases[i].b == ev) tb[i] = nd;
+            }
+        }
+    }
+    for (size_t i = 0; i < c->cap_phases.size(); ++i)
+        if (ta[i] && tb[i]) c->graph_tnodes.push_back({c->cap_phases[i].phase, ta[i], tb[i]});
+    e = c->cam_node ? cudaGraphInstantiate(&c->graph, g, 0) : cudaErrorInvalidValue;
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        c->graph = nullptr;
+        c->graph_tnodes.clear();
+        c->cam_node = nullptr;
+        return fail(c, GS_ERR_CUDA, "instantiating the mapping iteration graph failed", e);
+    }
+    c->graph_src = g;
+    c->graph_views = n_views;
+    c->graph_w = cams[0].width;
+    c->graph_h = cams[0].height;
+    c->graph_n = c->n;
+    c->graph_tile = c->tile;
+    c->graph_ppt = c->ppt;
+    c->graph_pair_cap = c->pair_cap;
+    c->graph_target = target;
+    c->graph_loss = loss_out;
+    c->graph_rgb = rgb;
+    c->graph_timing = c->timing;
+    return GS_OK;
 }
 
 int gs_timing_enable(gs_ctx* c, int enable) {

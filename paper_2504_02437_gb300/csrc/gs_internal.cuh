@@ -77,6 +77,7 @@ struct gs_ctx {
     int n_views = 0;            // views of the last render (0 = none)
     int width = 0, height = 0;  // size of every view of the last render
     int tile = 16;              // tile size of the last render
+    int ppt = 4;                // pixels per thread of the compositing kernels (1, 2 or 4; 8-px tiles: 1 or 2)
     int n_bins = 0;             // bins of the last render
     gs::DevCamera hcam[GS_MAX_VIEWS];
     gs::DevCamera* dcam = nullptr;          // [max_views]
@@ -107,17 +108,38 @@ struct gs_ctx {
     uint32_t* dcount = nullptr;             // device scalars: [0] pairs, [1] overflow
     uint32_t* hcount = nullptr;             // pinned host mirror
     float* partials = nullptr;              // reduction partials
+    float* fpart = nullptr;                 // photometric partials of the fused kernel (one per CTA)
+    int n_fpart = 0;
     int n_partials = 0;
     int num_sms = 0;
     int64_t launches = 0;                   // kernels launched by this context
 
     // iterate() graph cache
     cudaGraphExec_t graph = nullptr;
-    int graph_views = 0, graph_w = 0, graph_h = 0, graph_n = 0, graph_tile = 0;
+    cudaGraph_t graph_src = nullptr;        // kept alive: exec updates address its nodes
+    int graph_views = 0, graph_w = 0, graph_h = 0, graph_n = 0, graph_tile = 0, graph_ppt = 0;
+    bool graph_timing = false;
     int64_t graph_pair_cap = 0;
     const float* graph_target = nullptr;
     float* graph_loss = nullptr;
     float* graph_rgb = nullptr;
+    cudaStream_t cap_stream = nullptr;      // stream the iteration is captured on
+    cudaEvent_t graph_done = nullptr;       // recorded after each replay
+    bool graph_pending = false;             // a replay's flags have not been checked yet
+    uint32_t* hflags = nullptr;             // pinned: [0] pairs, [1] overflow of the last replay
+    cudaGraphNode_t cam_node = nullptr;     // kernel node that uploads the cameras
+    int64_t graph_kernels = 0;              // kernels per replay
+    bool capturing = false;
+    struct CapPhase {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<CapPhase> cap_phases;       // placeholder events recorded during capture
+    struct TimedNode {
+        int phase;
+        cudaGraphNode_t a, b;
+    };
+    std::vector<TimedNode> graph_tnodes;    // event-record nodes around each phase
     float* own_rgb = nullptr;               // internal image when the caller gives none
     size_t own_rgb_elems = 0;
     // phase timing (gs_timing_enable / gs_timing_read)
@@ -150,6 +172,13 @@ cudaError_t compute_ranges(gs_ctx* c, cudaStream_t s);
 cudaError_t launch_raster_forward(gs_ctx* c, const DevConst& k, float* rgb, int32_t* argmax, cudaStream_t s);
 cudaError_t launch_raster_backward(gs_ctx* c, const DevConst& k, const float* dLdC, cudaStream_t s);
 cudaError_t launch_count_work(gs_ctx* c, const DevConst& k, unsigned long long* out, cudaStream_t s);
+// forward + L1 loss + adjoint of every (view, tile) in one persistent launch; writes the image,
+// the screen-space gradients and one photometric partial per CTA (at most max_grid CTAs)
+cudaError_t launch_raster_fused(gs_ctx* c, const DevConst& k, const float* target, float* rgb, float* partials,
+                                int max_grid, int* grid_out, cudaStream_t s);
+// planar term partials + the final fixed-order sum of photometric and planar partials
+cudaError_t launch_loss_tail(gs_ctx* c, const DevConst& k, const float* photo_partials, int n_photo,
+                             float* loss_out, cudaStream_t s);
 cudaError_t launch_loss(gs_ctx* c, const DevConst& k, const float* rgb, const float* target, float* loss_out,
                         cudaStream_t s);
 cudaError_t launch_adam(gs_ctx* c, cudaStream_t s);

@@ -1,17 +1,21 @@
 // Front-to-back alpha compositing (Eq. 3, Section 3.1) and its adjoint.
 //
-// One CTA per (view, tile); one thread per pixel. Each warp owns an 8x4 pixel
-// block so that a Gaussian that misses the whole block can be skipped by the
-// warp. The tile's sorted pair list is walked in batches of one record per
-// thread staged in shared memory (gathered by Gaussian id from the 48-byte
-// raster records).
+// A persistent grid walks the (view, tile) work list; each thread owns PPT
+// pixels of one column of its tile, and each warp an 8 x (4 PPT) pixel block, so
+// a Gaussian that misses a warp's block costs that warp one test. The tile's
+// sorted pair list is walked in batches of records staged in shared memory
+// (gathered by Gaussian id from the 48-byte raster records).
 //
 // Membership is pixel-exact (|px - u| <= r and |py - v| <= r), so the image is
 // the same for every tile size: tiles only bound which Gaussians a pixel tests.
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gs {
 namespace {
+
+constexpr int kBatch = 256;   // records staged in shared memory per batch
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -19,233 +23,492 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// exponent of the Gaussian in base 2, written with explicit rounding so that the
-// forward and backward kernels take bit-identical alpha decisions
-__device__ __forceinline__ float power2(const float4 q, float dx, float dy) {
-    float t = __fmul_rn(__fmul_rn(q.z, dy), dy);
-    t = __fmaf_rn(__fmul_rn(q.y, dx), dy, t);
-    return __fmaf_rn(__fmul_rn(q.x, dx), dx, t);
-}
 
-// Stage one raster record relative to the local origin (ox, oy), the tile's
-// corner rounded down to a multiple of 32 px. The screen mean is stored split
-// (integer part in f0.xy, fractions in f1.w, f2.w); the local mean
-// (ui - ox) + uf is formed once per pair and tile, so pixel offsets carry the
-// rounding of a small number only, and the same for tiles of 8, 16 or 32 px
-// (which keeps the image bit-identical across tile sizes).
-__device__ __forceinline__ void load_record(const float4* __restrict__ rec, uint32_t item, float ox, float oy,
-                                            float4& s0, float4& s1, float4& s2) {
+// A raster record staged for one tile, relative to the local origin (ox, oy),
+// the tile's corner rounded down to a multiple of 32 px:
+//   s0 = {u, v, hx, hy}: local screen mean and the half-widths of the pixel
+//        box a pixel must lie in to be blended;
+//   s1 = {a', b', c', o}: exp2-scaled conic and opacity;
+//   s2 = {R, G, B, thr}: colour and the exponent threshold of the alpha cutoff.
+// The screen mean is stored split (integer part in f0.xy, fractions in f1.w,
+// f2.w); the local mean (ui - ox) + uf is formed once per pair and tile, so
+// pixel offsets carry the rounding of a small number only, and the same for
+// tiles of 8, 16 or 32 px (which keeps the image bit-identical across tile
+// sizes).
+//
+// Blending needs |dx| <= r, |dy| <= r (the membership box) and
+// o 2^p2 >= alpha_min, i.e. p2 >= thr = log2(alpha_min / o) with
+// p2 = a' dx^2 + b' dx dy + c' dy^2 (negative definite). The set p2 >= thr is
+// an ellipse whose axis-aligned half-widths are sqrt(-thr (B^-1)_xx),
+// sqrt(-thr (B^-1)_yy) with B = -[[a', b'/2], [b'/2, c']]; hx, hy are those
+// widths enlarged by 0.1 % + 0.01 px (far above float32 rounding) and capped
+// at r, so a pixel outside (hx, hy) cannot blend and skipping it leaves the
+// result unchanged. A Gaussian with o < alpha_min gets hx = hy = -1.
+__device__ __forceinline__ void stage_record(const float4* __restrict__ rec, uint32_t item, float ox, float oy,
+                                             float alpha_min, float4& s0, float4& s1, float4& s2) {
     const float4 a = rec[(size_t)item * 3 + 0];
     const float4 q = rec[(size_t)item * 3 + 1];
     const float4 c = rec[(size_t)item * 3 + 2];
-    s0 = make_float4((a.x - ox) + q.w, (a.y - oy) + c.w, a.z, a.w);
-    s1 = q;
-    s2 = c;
-}
-
-// pixel of thread `tid` inside a TILE x TILE tile: warps cover 8x4 blocks
-template <int TILE>
-__device__ __forceinline__ void pixel_of(int tid, int& lx, int& ly) {
-    constexpr int BX = TILE / 8;     // 8-wide blocks per tile row
-    int w = tid >> 5, l = tid & 31;
-    lx = (w % BX) * 8 + (l & 7);
-    ly = (w / BX) * 4 + (l >> 3);
-}
-
-template <int TILE>
-__global__ void __launch_bounds__(TILE* TILE) k_raster_fwd(const uint2* __restrict__ ranges,
-                                                           const uint32_t* __restrict__ pval,
-                                                           const float4* __restrict__ rec, int width, int height,
-                                                           int tiles_x, int tiles_per_view, int n, DevConst kc,
-                                                           float* __restrict__ out_rgb, float* __restrict__ out_T,
-                                                           uint32_t* __restrict__ out_last,
-                                                           int32_t* __restrict__ out_argmax) {
-    constexpr int BLOCK = TILE * TILE;
-    __shared__ float4 s0[BLOCK], s1[BLOCK], s2[BLOCK];
-    __shared__ uint32_t sid[BLOCK];
-    const int bin = blockIdx.x;
-    const int view = bin / tiles_per_view;
-    const int t = bin - view * tiles_per_view;
-    const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
-    int lx, ly;
-    pixel_of<TILE>(threadIdx.x, lx, ly);
-    const int px = txi * TILE + lx, py = tyi * TILE + ly;
-    const bool inside = px < width && py < height;
-    // pixel offsets are taken from a 32-px-aligned local origin (see load_record)
-    const float ox = (float)((txi * TILE) & ~31), oy = (float)((tyi * TILE) & ~31);
-    const float fx = (float)px - ox, fy = (float)py - oy;
-    const uint2 rg = ranges[bin];
-    float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f;
-    uint32_t last = 0;
-    float wmax = -1.f;
-    uint32_t amax = 0xFFFFFFFFu;
-    bool done = !inside;
-    for (uint32_t bs = rg.x; bs < rg.y; bs += BLOCK) {
-        if (__syncthreads_count(done) == BLOCK) break;
-        uint32_t j = bs + threadIdx.x;
-        if (j < rg.y) {
-            uint32_t item = pval[j];
-            load_record(rec, item, ox, oy, s0[threadIdx.x], s1[threadIdx.x], s2[threadIdx.x]);
-            sid[threadIdx.x] = item;
-        }
-        __syncthreads();
-        const int cnt = min((uint32_t)BLOCK, rg.y - bs);
-        for (int k = 0; k < cnt && !done; ++k) {
-            const float4 a = s0[k];
-            const float dx = fx - a.x, dy = fy - a.y;
-            if (fabsf(dx) > a.z || fabsf(dy) > a.z) continue;
-            const float4 q = s1[k];
-            const float alpha = fminf(kc.alpha_max, __fmul_rn(a.w, ex2_approx(power2(q, dx, dy))));
-            if (alpha < kc.alpha_min) continue;
-            const float Tn = __fmul_rn(T, 1.f - alpha);
-            if (Tn < kc.T_min) {
-                done = true;
-                break;
-            }
-            const float wgt = alpha * T;
-            const float4 c = s2[k];
-            cr = fmaf(c.x, wgt, cr);
-            cg = fmaf(c.y, wgt, cg);
-            cb = fmaf(c.z, wgt, cb);
-            T = Tn;
-            last = bs + k - rg.x + 1;
-            if (out_argmax != nullptr && wgt > wmax) {
-                wmax = wgt;
-                amax = sid[k];
-            }
+    const float r = a.z, o = a.w;
+    const float thr = log2f(alpha_min) - log2f(o);
+    float hx = -1.f, hy = -1.f;
+    if (thr <= 0.f) {
+        const float det = q.x * q.z - 0.25f * q.y * q.y;
+        if (det > 0.f) {
+            const float kap = -thr / det;
+            hx = fminf(fmaf(sqrtf(-kap * q.z), 1.001f, 0.01f), r);
+            hy = fminf(fmaf(sqrtf(-kap * q.x), 1.001f, 0.01f), r);
+        } else {
+            hx = hy = r;
         }
     }
-    if (inside) {
-        const size_t HW = (size_t)width * height;
-        const size_t pix = (size_t)py * width + px;
-        out_rgb[(size_t)view * 3 * HW + pix] = cr;
-        out_rgb[(size_t)view * 3 * HW + HW + pix] = cg;
-        out_rgb[(size_t)view * 3 * HW + 2 * HW + pix] = cb;
-        out_T[view * HW + pix] = T;
-        out_last[view * HW + pix] = last;
-        if (out_argmax != nullptr)
-            out_argmax[view * HW + pix] = amax == 0xFFFFFFFFu ? -1 : (int32_t)(amax - (uint32_t)view * n);
-    }
+    s0 = make_float4((a.x - ox) + q.w, (a.y - oy) + c.w, hx, hy);
+    s1 = make_float4(q.x, q.y, q.z, o);
+    s2 = make_float4(c.x, c.y, c.z, thr);
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Thread layout of a TILE x TILE tile: each thread owns PPT pixels of one
+// column, 4 rows apart; warp w owns an 8 x (4 PPT) block.
+template <int TILE, int PPT>
+struct Layout {
+    static constexpr int kThreads = TILE * TILE / PPT;
+    static constexpr int kBlocksX = TILE / 8;
+    __device__ static void pixel(int tid, int& lx, int& ly0) {
+        const int w = tid >> 5, l = tid & 31;
+        lx = (w % kBlocksX) * 8 + (l & 7);
+        ly0 = (w / kBlocksX) * (4 * PPT) + (l >> 3);
+    }
+};
+
+// Base-2 exponent a' dx^2 + b' dx dy + c' dy^2 of a Gaussian at a pixel,
+// written with explicit rounding so that every kernel takes bit-identical
+// decisions; the column part (a' dx and b' dx) is shared by a thread's pixels.
+__device__ __forceinline__ float power2_split(float qxdx, float qydx, float qz, float dx, float dy) {
+    float t = __fmul_rn(__fmul_rn(qz, dy), dy);
+    t = __fmaf_rn(qydx, dy, t);
+    return __fmaf_rn(qxdx, dx, t);
+}
+
+// Warp sum of 9 values by recursive halving: at each step a lane keeps half of
+// its values and trades the other half with its partner, so 9 values cost 11
+// exchanges instead of 45. Afterwards even lane L holds the full sum of value
+// *idx (or idx = -1 if its slot is padding); each value sits in exactly one
+// even lane.
+__device__ __forceinline__ float warp_sum9(const float (&v)[9], int lane, int& idx) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    float w[5];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    return v;
+    for (int i = 0; i < 5; ++i) {
+        const float a = v[i], b = (i + 5 < 9) ? v[i + 5] : 0.f;
+        w[i] = (b4 ? b : a) + __shfl_xor_sync(0xFFFFFFFFu, b4 ? a : b, 16);
+    }
+    float x[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float a = w[i], b = (i + 3 < 5) ? w[i + 3] : 0.f;
+        x[i] = (b3 ? b : a) + __shfl_xor_sync(0xFFFFFFFFu, b3 ? a : b, 8);
+    }
+    float y[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float a = x[i], b = (i + 2 < 3) ? x[i + 2] : 0.f;
+        y[i] = (b2 ? b : a) + __shfl_xor_sync(0xFFFFFFFFu, b2 ? a : b, 4);
+    }
+    float z = (b1 ? y[1] : y[0]) + __shfl_xor_sync(0xFFFFFFFFu, b1 ? y[0] : y[1], 2);
+    z += __shfl_xor_sync(0xFFFFFFFFu, z, 1);
+    const int s3 = b2 ? 2 : 0, s4 = b1 ? 1 : 0;
+    const int local = (b3 ? 3 : 0) + s3 + s4;
+    const int id = (b4 ? 5 : 0) + local;
+    idx = ((lane & 1) == 0 && s3 + s4 < 3 && local < 5 && id < 9) ? id : -1;
+    return z;
 }
 
-template <int TILE>
-__global__ void __launch_bounds__(TILE* TILE) k_raster_bwd(const uint2* __restrict__ ranges,
-                                                           const uint32_t* __restrict__ pval,
-                                                           const float4* __restrict__ rec, int width, int height,
-                                                           int tiles_x, int tiles_per_view, DevConst kc,
-                                                           const float* __restrict__ T_final,
-                                                           const uint32_t* __restrict__ n_last,
-                                                           const float* __restrict__ dLdC,
-                                                           float* __restrict__ grad2d) {
-    constexpr int BLOCK = TILE * TILE;
-    __shared__ float4 s0[BLOCK], s1[BLOCK], s2[BLOCK];
-    __shared__ uint32_t sid[BLOCK];
-    __shared__ uint32_t smax;
-    const int bin = blockIdx.x;
-    const int view = bin / tiles_per_view;
-    const int t = bin - view * tiles_per_view;
-    const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
-    int lx, ly;
-    pixel_of<TILE>(threadIdx.x, lx, ly);
-    const int px = txi * TILE + lx, py = tyi * TILE + ly;
-    const bool inside = px < width && py < height;
-    const float ox = (float)((txi * TILE) & ~31), oy = (float)((tyi * TILE) & ~31);
-    const float fx = (float)px - ox, fy = (float)py - oy;
-    const uint2 rg = ranges[bin];
-    const size_t HW = (size_t)width * height;
-    const size_t pix = (size_t)py * width + px;
-    float T = 1.f, gr = 0.f, gg = 0.f, gb = 0.f;
-    uint32_t mine = 0;
-    if (inside) {
-        T = T_final[view * HW + pix];
-        mine = n_last[view * HW + pix];
-        gr = dLdC[(size_t)view * 3 * HW + pix];
-        gg = dLdC[(size_t)view * 3 * HW + HW + pix];
-        gb = dLdC[(size_t)view * 3 * HW + 2 * HW + pix];
+// Shared-memory staging of one batch of raster records, shared by the forward
+// and backward passes of a CTA.
+struct Stage {
+    float4 s0[kBatch], s1[kBatch], s2[kBatch];
+    uint32_t sid[kBatch];
+    uint32_t mask[kBatch];   // bit w: the record's pixel box meets warp w's pixel block
+};
+__device__ __forceinline__ Stage& stage() {
+    __shared__ Stage st;
+    return st;
+}
+
+// Geometry of one work item (a tile of one view) as seen by one thread.
+template <int TILE, int PPT>
+struct TileGeom {
+    int view, txi, tyi, px, py0;
+    float ox, oy, fx;
+    uint2 rg;
+    __device__ TileGeom(int bin, const uint2* __restrict__ ranges, int tiles_x, int tiles_per_view) {
+        view = bin / tiles_per_view;
+        const int t = bin - view * tiles_per_view;
+        tyi = t / tiles_x;
+        txi = t - tyi * tiles_x;
+        int lx, ly0;
+        Layout<TILE, PPT>::pixel(threadIdx.x, lx, ly0);
+        px = txi * TILE + lx;
+        py0 = tyi * TILE + ly0;
+        // pixel offsets are taken from a 32-px-aligned local origin (see load_record)
+        ox = (float)((txi * TILE) & ~31);
+        oy = (float)((tyi * TILE) & ~31);
+        fx = (float)px - ox;
+        rg = ranges[bin];
     }
-    if (threadIdx.x == 0) smax = 0;
-    __syncthreads();
-    uint32_t wm = __reduce_max_sync(0xFFFFFFFFu, mine);
-    if ((threadIdx.x & 31) == 0) atomicMax(&smax, wm);
-    __syncthreads();
-    const uint32_t end = rg.x + smax;
-    const uint32_t my_end = rg.x + mine;     // entries at positions < my_end may blend
-    float ar = 0.f, ag = 0.f, ab = 0.f;      // colour accumulated behind, normalised by T
-    for (uint32_t be = end; be > rg.x;) {
-        const uint32_t bs = be > rg.x + BLOCK ? be - BLOCK : rg.x;
-        __syncthreads();
-        uint32_t j = bs + threadIdx.x;
-        if (j < be) {
-            uint32_t item = pval[j];
-            load_record(rec, item, ox, oy, s0[threadIdx.x], s1[threadIdx.x], s2[threadIdx.x]);
-            sid[threadIdx.x] = item;
+    __device__ int py(int p) const { return py0 + 4 * p; }
+};
+
+// Warps of the CTA whose 8 x (4 PPT) pixel block meets the box u +- hx, v +- hy.
+template <int TILE, int PPT>
+__device__ __forceinline__ uint32_t warp_mask(const TileGeom<TILE, PPT>& g, const float4 s0) {
+    constexpr int NW = Layout<TILE, PPT>::kThreads / 32;
+    constexpr int BX = Layout<TILE, PPT>::kBlocksX;
+    const float tox = (float)(g.txi * TILE) - g.ox, toy = (float)(g.tyi * TILE) - g.oy;
+    // widened by 0.01 px so that rounding cannot drop a pixel the per-pixel test would keep
+    const float x0 = s0.x - s0.z - 0.01f, x1 = s0.x + s0.z + 0.01f, y0 = s0.y - s0.w - 0.01f,
+                y1 = s0.y + s0.w + 0.01f;
+    uint32_t m = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const float bx = tox + 8.f * (float)(w % BX), by = toy + (float)(4 * PPT) * (float)(w / BX);
+        const bool hit = x0 <= bx + 7.f && x1 >= bx && y0 <= by + (float)(4 * PPT - 1) && y1 >= by;
+        m |= hit ? (1u << w) : 0u;
+    }
+    return m;
+}
+
+// Forward compositing (Eq. 3) of a thread's PPT pixels over the tile's sorted
+// list. Returns final T, the colour, and per pixel the number of list entries
+// up to and including the last blended Gaussian; optionally the Eq. 8 argmax.
+template <int TILE, int PPT, bool ARGMAX>
+__device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const bool (&inside)[PPT],
+                                         const uint32_t* __restrict__ pval, const float4* __restrict__ rec,
+                                         const DevConst& kc, float (&T)[PPT], float (&cr)[PPT], float (&cg)[PPT],
+                                         float (&cb)[PPT], uint32_t (&last)[PPT], uint32_t (&amax)[PPT]) {
+    constexpr int NT = Layout<TILE, PPT>::kThreads;
+    Stage& st = stage();
+    float4* s0 = st.s0;
+    float4* s1 = st.s1;
+    float4* s2 = st.s2;
+    uint32_t* sid = st.sid;
+    float fy[PPT], wmax[PPT];
+    bool live[PPT];
+    int nlive = 0;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        fy[p] = (float)g.py(p) - g.oy;
+        live[p] = inside[p];
+        nlive += live[p] ? 1 : 0;
+        T[p] = 1.f;
+        cr[p] = cg[p] = cb[p] = 0.f;
+        last[p] = 0;
+        wmax[p] = -1.f;
+        amax[p] = 0xFFFFFFFFu;
+    }
+    const uint2 rg = g.rg;
+    for (uint32_t bs = rg.x; bs < rg.y; bs += kBatch) {
+        if (__syncthreads_count(nlive > 0) == 0) break;
+        for (int i = threadIdx.x; i < kBatch; i += NT) {
+            const uint32_t j = bs + i;
+            if (j < rg.y) {
+                const uint32_t item = pval[j];
+                stage_record(rec, item, g.ox, g.oy, kc.alpha_min, s0[i], s1[i], s2[i]);
+                sid[i] = item;
+                st.mask[i] = warp_mask<TILE, PPT>(g, s0[i]);
+            }
         }
         __syncthreads();
-        for (int k = (int)(be - bs) - 1; k >= 0; --k) {
-            const uint32_t pos = bs + k;
+        const int cnt = min((uint32_t)kBatch, rg.y - bs);
+        const uint32_t wbit = 1u << (threadIdx.x >> 5);
+        for (int k = 0; k < cnt && nlive > 0; ++k) {
+            if (!(st.mask[k] & wbit)) continue;
             const float4 a = s0[k];
-            const float dx = fx - a.x, dy = fy - a.y;
-            bool contrib = pos < my_end && fabsf(dx) <= a.z && fabsf(dy) <= a.z;
+            const float dx = g.fx - a.x;
+            if (fabsf(dx) > a.z) continue;
             const float4 q = s1[k];
-            const float G = ex2_approx(power2(q, dx, dy));
-            const float oG = __fmul_rn(a.w, G);
-            const float alpha = fminf(kc.alpha_max, oG);
-            contrib = contrib && alpha >= kc.alpha_min;
-            if (!__any_sync(0xFFFFFFFFu, contrib)) continue;
-            float g_u = 0.f, g_v = 0.f, g_a = 0.f, g_b = 0.f, g_c = 0.f, g_o = 0.f, g_r = 0.f, g_g = 0.f, g_bb = 0.f;
-            if (contrib) {
+            const float thr = s2[k].w;
+            const float qxdx = __fmul_rn(q.x, dx), qydx = __fmul_rn(q.y, dx);
+#pragma unroll
+            for (int p = 0; p < PPT; ++p) {
+                if (!live[p]) continue;
+                const float dy = fy[p] - a.y;
+                if (fabsf(dy) > a.w) continue;
+                const float p2 = power2_split(qxdx, qydx, q.z, dx, dy);
+                if (p2 < thr) continue;
+                const float alpha = fminf(kc.alpha_max, __fmul_rn(q.w, ex2_approx(p2)));
+                const float Tn = __fmul_rn(T[p], 1.f - alpha);
+                if (Tn < kc.T_min) {
+                    live[p] = false;
+                    --nlive;
+                    continue;
+                }
+                const float wgt = alpha * T[p];
                 const float4 c = s2[k];
-                const float oma = 1.f - alpha;
-                T = T / oma;                             // transmittance in front of this Gaussian
-                const float wgt = alpha * T;
-                g_r = gr * wgt;
-                g_g = gg * wgt;
-                g_bb = gb * wgt;
-                const float dalpha = T * (gr * (c.x - ar) + gg * (c.y - ag) + gb * (c.z - ab));
-                ar = fmaf(alpha, c.x - ar, ar);
-                ag = fmaf(alpha, c.y - ag, ag);
-                ab = fmaf(alpha, c.z - ab, ab);
-                if (oG <= kc.alpha_max) {
-                    // dL/dp2 with alpha = o 2^p2
-                    const float g2 = dalpha * oG * kLn2;
-                    g_u = -g2 * (2.f * q.x * dx + q.y * dy);
-                    g_v = -g2 * (q.y * dx + 2.f * q.z * dy);
-                    g_a = g2 * dx * dx;
-                    g_b = g2 * dx * dy;
-                    g_c = g2 * dy * dy;
-                    g_o = dalpha * G;
+                cr[p] = fmaf(c.x, wgt, cr[p]);
+                cg[p] = fmaf(c.y, wgt, cg[p]);
+                cb[p] = fmaf(c.z, wgt, cb[p]);
+                T[p] = Tn;
+                last[p] = bs + k - rg.x + 1;
+                if (ARGMAX && wgt > wmax[p]) {
+                    wmax[p] = wgt;
+                    amax[p] = sid[k];
                 }
             }
-            g_u = warp_sum(g_u);
-            g_v = warp_sum(g_v);
-            g_a = warp_sum(g_a);
-            g_b = warp_sum(g_b);
-            g_c = warp_sum(g_c);
-            g_o = warp_sum(g_o);
-            g_r = warp_sum(g_r);
-            g_g = warp_sum(g_g);
-            g_bb = warp_sum(g_bb);
-            if ((threadIdx.x & 31) == 0) {
-                float* dst = grad2d + (size_t)sid[k] * kGrad2dStride;
-                atomicAdd(reinterpret_cast<float4*>(dst), make_float4(g_u, g_v, g_a, g_b));
-                atomicAdd(reinterpret_cast<float4*>(dst + 4), make_float4(g_c, g_o, g_r, g_g));
-                atomicAdd(dst + 8, g_bb);
+        }
+    }
+}
+
+// Adjoint of the compositing for a thread's PPT pixels: walks the tile's list
+// back to front from the block's largest last-blended entry, recovering
+// T_i = T_{i+1} / (1 - alpha_i) from the final T, and accumulates the
+// gradients w.r.t. each Gaussian's screen quantities (warp sum, then one
+// 9-lane atomic per Gaussian and warp).
+template <int TILE, int PPT>
+__device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uint32_t* __restrict__ pval,
+                                         const float4* __restrict__ rec, const DevConst& kc, float (&T)[PPT],
+                                         const uint32_t (&cnt_last)[PPT], const float (&gr)[PPT],
+                                         const float (&gg)[PPT], const float (&gb)[PPT],
+                                         float* __restrict__ grad2d) {
+    constexpr int NT = Layout<TILE, PPT>::kThreads;
+    Stage& st = stage();
+    float4* s0 = st.s0;
+    float4* s1 = st.s1;
+    float4* s2 = st.s2;
+    uint32_t* sid = st.sid;
+    __shared__ uint32_t smax;
+    const int lane = threadIdx.x & 31;
+    const uint2 rg = g.rg;
+    float fy[PPT], ar[PPT], ag[PPT], ab[PPT];
+    uint32_t my_end[PPT];
+    uint32_t thread_end = rg.x;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+        fy[p] = (float)g.py(p) - g.oy;
+        ar[p] = ag[p] = ab[p] = 0.f;
+        my_end[p] = rg.x + cnt_last[p];
+        thread_end = max(thread_end, my_end[p]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) smax = rg.x;
+    __syncthreads();
+    const uint32_t wm = __reduce_max_sync(0xFFFFFFFFu, thread_end);
+    if (lane == 0) atomicMax(&smax, wm);
+    __syncthreads();
+    const uint32_t end = smax;
+    for (uint32_t be = end; be > rg.x;) {
+        const uint32_t bs = be - rg.x > (uint32_t)kBatch ? be - kBatch : rg.x;
+        __syncthreads();
+        for (int i = threadIdx.x; i < kBatch; i += NT) {
+            const uint32_t j = bs + i;
+            if (j < be) {
+                const uint32_t item = pval[j];
+                stage_record(rec, item, g.ox, g.oy, kc.alpha_min, s0[i], s1[i], s2[i]);
+                sid[i] = item;
+                st.mask[i] = warp_mask<TILE, PPT>(g, s0[i]);
             }
+        }
+        __syncthreads();
+        const uint32_t wbit = 1u << (threadIdx.x >> 5);
+        for (int k = (int)(be - bs) - 1; k >= 0; --k) {
+            if (!(st.mask[k] & wbit)) continue;
+            const uint32_t pos = bs + k;
+            const float4 a = s0[k];
+            const float dx = g.fx - a.x;
+            const bool col = fabsf(dx) <= a.z && pos < thread_end;
+            if (!__any_sync(0xFFFFFFFFu, col)) continue;
+            float acc[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) acc[i] = 0.f;
+            bool any = false;
+            if (col) {
+                const float4 q = s1[k];
+                const float4 c = s2[k];
+                const float qxdx = __fmul_rn(q.x, dx), qydx = __fmul_rn(q.y, dx);
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) {
+                    const float dy = fy[p] - a.y;
+                    if (pos >= my_end[p] || fabsf(dy) > a.w) continue;
+                    const float p2 = power2_split(qxdx, qydx, q.z, dx, dy);
+                    if (p2 < c.w) continue;
+                    const float G = ex2_approx(p2);
+                    const float oG = __fmul_rn(q.w, G);
+                    const float alpha = fminf(kc.alpha_max, oG);
+                    any = true;
+                    const float oma = 1.f - alpha;       // >= 1 - alpha_max = 0.01
+                    T[p] = __fdividef(T[p], oma);        // transmittance in front of this Gaussian (2 ulp)
+                    const float wgt = alpha * T[p];
+                    acc[6] = fmaf(gr[p], wgt, acc[6]);
+                    acc[7] = fmaf(gg[p], wgt, acc[7]);
+                    acc[8] = fmaf(gb[p], wgt, acc[8]);
+                    const float dalpha = T[p] * (gr[p] * (c.x - ar[p]) + gg[p] * (c.y - ag[p]) + gb[p] * (c.z - ab[p]));
+                    ar[p] = fmaf(alpha, c.x - ar[p], ar[p]);
+                    ag[p] = fmaf(alpha, c.y - ag[p], ag[p]);
+                    ab[p] = fmaf(alpha, c.z - ab[p], ab[p]);
+                    if (oG <= kc.alpha_max) {
+                        // dL/dp2 with alpha = o 2^p2
+                        const float g2 = dalpha * oG * kLn2;
+                        acc[0] -= g2 * (2.f * q.x * dx + q.y * dy);
+                        acc[1] -= g2 * (q.y * dx + 2.f * q.z * dy);
+                        acc[2] = fmaf(g2 * dx, dx, acc[2]);
+                        acc[3] = fmaf(g2 * dx, dy, acc[3]);
+                        acc[4] = fmaf(g2 * dy, dy, acc[4]);
+                        acc[5] = fmaf(dalpha, G, acc[5]);
+                    }
+                }
+            }
+            if (!__any_sync(0xFFFFFFFFu, any)) continue;
+            int idx;
+            const float v = warp_sum9(acc, lane, idx);
+            if (idx >= 0) atomicAdd(grad2d + (size_t)sid[k] * kGrad2dStride + idx, v);
         }
         be = bs;
     }
 }
 
+// Persistent compositing kernels: a grid sized to the GPU's resident capacity
+// walks the (view, tile) work list through an atomic counter, so the load
+// stays balanced across tiles of very different cost and across the views of
+// a window. `order` (optional) lists the bins in the order to take them.
+__device__ __forceinline__ bool next_work(uint32_t* __restrict__ queue, uint32_t n_items,
+                                          const uint32_t* __restrict__ order, int& bin) {
+    __shared__ uint32_t s_work;
+    __syncthreads();
+    if (threadIdx.x == 0) s_work = atomicAdd(queue, 1u);
+    __syncthreads();
+    const uint32_t w = s_work;
+    if (w >= n_items) return false;
+    bin = order ? (int)order[w] : (int)w;
+    return true;
+}
+
+template <int TILE, int PPT>
+__device__ __forceinline__ void inside_mask(const TileGeom<TILE, PPT>& g, int width, int height, bool (&inside)[PPT]) {
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) inside[p] = g.px < width && g.py(p) < height;
+}
+
+template <int TILE, int PPT, bool ARGMAX>
+__global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
+    k_raster_fwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ pval, const float4* __restrict__ rec,
+                 int width, int height, int tiles_x, int tiles_per_view, int n, DevConst kc,
+                 float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_last,
+                 int32_t* __restrict__ out_argmax, uint32_t* __restrict__ queue, uint32_t n_items,
+                 const uint32_t* __restrict__ order) {
+    int bin;
+    const size_t HW = (size_t)width * height;
+    while (next_work(queue, n_items, order, bin)) {
+        const TileGeom<TILE, PPT> g(bin, ranges, tiles_x, tiles_per_view);
+        bool inside[PPT];
+        inside_mask(g, width, height, inside);
+        float T[PPT], cr[PPT], cg[PPT], cb[PPT];
+        uint32_t last[PPT], amax[PPT];
+        fwd_core<TILE, PPT, ARGMAX>(g, inside, pval, rec, kc, T, cr, cg, cb, last, amax);
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            if (!inside[p]) continue;
+            const size_t pix = (size_t)g.py(p) * width + g.px;
+            out_rgb[(size_t)g.view * 3 * HW + pix] = cr[p];
+            out_rgb[(size_t)g.view * 3 * HW + HW + pix] = cg[p];
+            out_rgb[(size_t)g.view * 3 * HW + 2 * HW + pix] = cb[p];
+            out_T[g.view * HW + pix] = T[p];
+            out_last[g.view * HW + pix] = last[p];
+            if (ARGMAX)
+                out_argmax[g.view * HW + pix] =
+                    amax[p] == 0xFFFFFFFFu ? -1 : (int32_t)(amax[p] - (uint32_t)g.view * n);
+        }
+    }
+}
+
+template <int TILE, int PPT>
+__global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
+    k_raster_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ pval, const float4* __restrict__ rec,
+                 int width, int height, int tiles_x, int tiles_per_view, DevConst kc,
+                 const float* __restrict__ T_final, const uint32_t* __restrict__ n_last,
+                 const float* __restrict__ dLdC, float* __restrict__ grad2d, uint32_t* __restrict__ queue,
+                 uint32_t n_items, const uint32_t* __restrict__ order) {
+    int bin;
+    const size_t HW = (size_t)width * height;
+    while (next_work(queue, n_items, order, bin)) {
+        const TileGeom<TILE, PPT> g(bin, ranges, tiles_x, tiles_per_view);
+        float T[PPT], gr[PPT], gg[PPT], gb[PPT];
+        uint32_t cnt[PPT];
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            T[p] = 1.f;
+            gr[p] = gg[p] = gb[p] = 0.f;
+            cnt[p] = 0;
+            if (g.px < width && g.py(p) < height) {
+                const size_t pix = (size_t)g.py(p) * width + g.px;
+                T[p] = T_final[g.view * HW + pix];
+                cnt[p] = n_last[g.view * HW + pix];
+                gr[p] = dLdC[(size_t)g.view * 3 * HW + pix];
+                gg[p] = dLdC[(size_t)g.view * 3 * HW + HW + pix];
+                gb[p] = dLdC[(size_t)g.view * 3 * HW + 2 * HW + pix];
+            }
+        }
+        bwd_core<TILE, PPT>(g, pval, rec, kc, T, cnt, gr, gg, gb, grad2d);
+    }
+}
+
+// One mapping iteration's compositing for every (view, tile): forward (Eq. 3),
+// the L1 term of Eq. 10 and dL/dC = lambda sign(C - I) / 3HW for the tile's
+// pixels, then the adjoint, with final T, last index and dL/dC kept in
+// registers. Writes the image and one photometric partial sum per CTA.
+template <int TILE, int PPT>
+__global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
+    k_raster_fused(const uint2* __restrict__ ranges, const uint32_t* __restrict__ pval,
+                   const float4* __restrict__ rec, int width, int height, int tiles_x, int tiles_per_view,
+                   DevConst kc, const float* __restrict__ target, float scale, float* __restrict__ out_rgb,
+                   float* __restrict__ grad2d, float* __restrict__ partials, uint32_t* __restrict__ queue,
+                   uint32_t n_items, const uint32_t* __restrict__ order) {
+    int bin;
+    const size_t HW = (size_t)width * height;
+    float loss = 0.f;
+    while (next_work(queue, n_items, order, bin)) {
+        const TileGeom<TILE, PPT> g(bin, ranges, tiles_x, tiles_per_view);
+        bool inside[PPT];
+        inside_mask(g, width, height, inside);
+        float T[PPT], cr[PPT], cg[PPT], cb[PPT], gr[PPT], gg[PPT], gb[PPT];
+        uint32_t last[PPT], amax[PPT];
+        fwd_core<TILE, PPT, false>(g, inside, pval, rec, kc, T, cr, cg, cb, last, amax);
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            gr[p] = gg[p] = gb[p] = 0.f;
+            if (!inside[p]) {
+                last[p] = 0;
+                continue;
+            }
+            const size_t pix = (size_t)g.py(p) * width + g.px;
+            const size_t o = (size_t)g.view * 3 * HW + pix;
+            out_rgb[o] = cr[p];
+            out_rgb[o + HW] = cg[p];
+            out_rgb[o + 2 * HW] = cb[p];
+            const float r0 = cr[p] - target[o], r1 = cg[p] - target[o + HW], r2 = cb[p] - target[o + 2 * HW];
+            loss += (fabsf(r0) + fabsf(r1)) + fabsf(r2);
+            gr[p] = scale * (float)((r0 > 0.f) - (r0 < 0.f));
+            gg[p] = scale * (float)((r1 > 0.f) - (r1 < 0.f));
+            gb[p] = scale * (float)((r2 > 0.f) - (r2 < 0.f));
+        }
+        bwd_core<TILE, PPT>(g, pval, rec, kc, T, last, gr, gg, gb, grad2d);
+    }
+    // per-CTA photometric partial (already scaled)
+    __shared__ float red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xFFFFFFFFu, loss, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = loss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        partials[blockIdx.x] = t * scale;
+    }
+}
+
 // Algorithmic work of the last render, by replaying the forward traversal per
-// pixel: out[0] += pairs tested by the forward pass (up to and including the
-// stopping one), out[1] += pairs blended, out[2] += pairs the backward pass
-// walks (entries up to the last blended one).
+// pixel: out[0] += list entries the forward pass reaches (up to and including
+// the stopping one), out[1] += pairs blended, out[2] += list entries the
+// backward pass reaches (up to the last blended one).
 template <int TILE>
 __global__ void __launch_bounds__(TILE* TILE) k_count_work(const uint2* __restrict__ ranges,
                                                            const float4* __restrict__ rec,
@@ -256,8 +519,7 @@ __global__ void __launch_bounds__(TILE* TILE) k_count_work(const uint2* __restri
     const int view = bin / tiles_per_view;
     const int t = bin - view * tiles_per_view;
     const int tyi = t / tiles_x, txi = t - tyi * tiles_x;
-    int lx, ly;
-    pixel_of<TILE>(threadIdx.x, lx, ly);
+    const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
     const int px = txi * TILE + lx, py = tyi * TILE + ly;
     if (px >= width || py >= height) return;
     const float ox = (float)((txi * TILE) & ~31), oy = (float)((tyi * TILE) & ~31);
@@ -268,12 +530,13 @@ __global__ void __launch_bounds__(TILE* TILE) k_count_work(const uint2* __restri
     for (uint32_t j = rg.x; j < rg.y; ++j) {
         const uint32_t item = pval[j];
         float4 a, q, c;
-        load_record(rec, item, ox, oy, a, q, c);
+        stage_record(rec, item, ox, oy, kc.alpha_min, a, q, c);
         ++tested;
         const float dx = fx - a.x, dy = fy - a.y;
-        if (fabsf(dx) > a.z || fabsf(dy) > a.z) continue;
-        const float alpha = fminf(kc.alpha_max, __fmul_rn(a.w, ex2_approx(power2(q, dx, dy))));
-        if (alpha < kc.alpha_min) continue;
+        if (fabsf(dx) > a.z || fabsf(dy) > a.w) continue;
+        const float p2 = power2_split(__fmul_rn(q.x, dx), __fmul_rn(q.y, dx), q.z, dx, dy);
+        if (p2 < c.w) continue;
+        const float alpha = fminf(kc.alpha_max, __fmul_rn(q.w, ex2_approx(p2)));
         const float Tn = __fmul_rn(T, 1.f - alpha);
         if (Tn < kc.T_min) break;
         T = Tn;
@@ -300,33 +563,101 @@ cudaError_t launch_count_work(gs_ctx* c, const DevConst& k, unsigned long long* 
     return cudaGetLastError();
 }
 
+// resident CTAs of a kernel on the whole GPU (cached per kernel instantiation)
+template <int KIND, int TILE, int PPT, typename K>
+static int resident_grid(K kernel, int threads, int num_sms) {
+    static int cached = 0;
+    if (cached == 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        cached = per_sm * num_sms;
+    }
+    return cached;
+}
+
+template <int TILE, int PPT>
+static void fwd_launch(gs_ctx* c, const DevConst& k, float* rgb, int32_t* argmax, cudaStream_t s, int tpv) {
+    constexpr int NT = Layout<TILE, PPT>::kThreads;
+    if (argmax) {
+        const int grid = std::min(resident_grid<0, TILE, PPT>(k_raster_fwd<TILE, PPT, true>, NT, c->num_sms), c->n_bins);
+        k_raster_fwd<TILE, PPT, true><<<grid, NT, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width, c->height,
+                                                          c->hcam[0].tiles_x, tpv, c->n, k, rgb, c->T_final,
+                                                          c->n_last, argmax, c->dcount + 6, (uint32_t)c->n_bins,
+                                                          nullptr);
+    } else {
+        const int grid =
+            std::min(resident_grid<1, TILE, PPT>(k_raster_fwd<TILE, PPT, false>, NT, c->num_sms), c->n_bins);
+        k_raster_fwd<TILE, PPT, false><<<grid, NT, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width,
+                                                           c->height, c->hcam[0].tiles_x, tpv, c->n, k, rgb,
+                                                           c->T_final, c->n_last, nullptr, c->dcount + 6,
+                                                           (uint32_t)c->n_bins, nullptr);
+    }
+}
+
+template <int TILE, int PPT>
+static void bwd_launch(gs_ctx* c, const DevConst& k, const float* dLdC, cudaStream_t s, int tpv) {
+    constexpr int NT = Layout<TILE, PPT>::kThreads;
+    const int grid = std::min(resident_grid<2, TILE, PPT>(k_raster_bwd<TILE, PPT>, NT, c->num_sms), c->n_bins);
+    k_raster_bwd<TILE, PPT><<<grid, NT, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width, c->height,
+                                                c->hcam[0].tiles_x, tpv, k, c->T_final, c->n_last, dLdC, c->grad2d,
+                                                c->dcount + 7, (uint32_t)c->n_bins, nullptr);
+}
+
+template <int TILE, int PPT>
+static void fused_launch(gs_ctx* c, const DevConst& k, const float* target, float* rgb, cudaStream_t s, int tpv,
+                         float* partials, int max_grid, int* grid_out) {
+    constexpr int NT = Layout<TILE, PPT>::kThreads;
+    const int grid = std::min(std::min(resident_grid<3, TILE, PPT>(k_raster_fused<TILE, PPT>, NT, c->num_sms),
+                                       c->n_bins), max_grid);
+    const float scale = k.lambda_color / (float)(3 * (size_t)c->width * c->height);
+    k_raster_fused<TILE, PPT><<<grid, NT, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width, c->height,
+                                                  c->hcam[0].tiles_x, tpv, k, target, scale, rgb, c->grad2d, partials,
+                                                  c->dcount + 6, (uint32_t)c->n_bins, nullptr);
+    *grid_out = grid;
+}
+
+#define GS_DISPATCH(FN, ...)                                         \
+    do {                                                             \
+        if (c->tile == 16) {                                         \
+            if (c->ppt == 1) FN<16, 1>(__VA_ARGS__);                 \
+            else if (c->ppt == 2) FN<16, 2>(__VA_ARGS__);            \
+            else FN<16, 4>(__VA_ARGS__);                             \
+        } else {                                                     \
+            if (c->ppt == 1) FN<8, 1>(__VA_ARGS__);                  \
+            else FN<8, 2>(__VA_ARGS__);                              \
+        }                                                            \
+    } while (0)
+
 cudaError_t launch_raster_forward(gs_ctx* c, const DevConst& k, float* rgb, int32_t* argmax, cudaStream_t s) {
     const int tpv = c->hcam[0].tiles_x * c->hcam[0].tiles_y;
     if (c->n_bins == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(c->dcount + 6, 0, sizeof(uint32_t), s);   // work queue
+    if (e != cudaSuccess) return e;
     ++c->launches;
-    if (c->tile == 16)
-        k_raster_fwd<16><<<c->n_bins, 256, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width, c->height,
-                                                   c->hcam[0].tiles_x, tpv, c->n, k, rgb, c->T_final, c->n_last,
-                                                   argmax);
-    else
-        k_raster_fwd<8><<<c->n_bins, 64, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width, c->height,
-                                                 c->hcam[0].tiles_x, tpv, c->n, k, rgb, c->T_final, c->n_last,
-                                                 argmax);
+    GS_DISPATCH(fwd_launch, c, k, rgb, argmax, s, tpv);
     return cudaGetLastError();
 }
 
 cudaError_t launch_raster_backward(gs_ctx* c, const DevConst& k, const float* dLdC, cudaStream_t s) {
     const int tpv = c->hcam[0].tiles_x * c->hcam[0].tiles_y;
     if (c->n_bins == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(c->dcount + 7, 0, sizeof(uint32_t), s);   // work queue
+    if (e != cudaSuccess) return e;
     ++c->launches;
-    if (c->tile == 16)
-        k_raster_bwd<16><<<c->n_bins, 256, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width, c->height,
-                                                   c->hcam[0].tiles_x, tpv, k, c->T_final, c->n_last, dLdC,
-                                                   c->grad2d);
-    else
-        k_raster_bwd<8><<<c->n_bins, 64, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width, c->height,
-                                                 c->hcam[0].tiles_x, tpv, k, c->T_final, c->n_last, dLdC,
-                                                 c->grad2d);
+    GS_DISPATCH(bwd_launch, c, k, dLdC, s, tpv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_raster_fused(gs_ctx* c, const DevConst& k, const float* target, float* rgb, float* partials,
+                                int max_grid, int* grid_out, cudaStream_t s) {
+    const int tpv = c->hcam[0].tiles_x * c->hcam[0].tiles_y;
+    *grid_out = 0;
+    if (c->n_bins == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(c->dcount + 6, 0, sizeof(uint32_t), s);   // work queue
+    if (e != cudaSuccess) return e;
+    ++c->launches;
+    GS_DISPATCH(fused_launch, c, k, target, rgb, s, tpv, partials, max_grid, grid_out);
     return cudaGetLastError();
 }
 

@@ -17,15 +17,29 @@ __device__ __forceinline__ float block_sum(float v, float* sh) {
     return t;   // valid in thread 0
 }
 
-// L1 photometric term: per-block partial sums of |C - I| (each view's sum is
-// scaled by lambda_color / 3HW), and dL/dC = lambda_color sign(C - I) / 3HW.
+// L1 photometric term: per-block partial sums of |C - I| (scaled by
+// lambda_color / 3HW), and dL/dC = lambda_color sign(C - I) / 3HW. Vectorised
+// by float4 over the flat [V][3][H][W] arrays; `total` is a multiple of 4 here
+// and the tail (if any) is handled by the scalar loop.
 __global__ void __launch_bounds__(kRedThreads) k_l1(const float* __restrict__ rgb, const float* __restrict__ tgt,
                                                     size_t total, float scale, float* __restrict__ dLdC,
                                                     float* __restrict__ partials) {
     __shared__ float sh[kRedThreads / 32];
     float acc = 0.f;
-    for (size_t i = blockIdx.x * (size_t)kRedThreads + threadIdx.x; i < total; i += (size_t)gridDim.x * kRedThreads) {
-        float r = rgb[i] - tgt[i];
+    const size_t n4 = total / 4;
+    const size_t stride = (size_t)gridDim.x * kRedThreads;
+    const float4* r4 = reinterpret_cast<const float4*>(rgb);
+    const float4* t4 = reinterpret_cast<const float4*>(tgt);
+    float4* d4 = reinterpret_cast<float4*>(dLdC);
+    for (size_t i = blockIdx.x * (size_t)kRedThreads + threadIdx.x; i < n4; i += stride) {
+        const float4 a = r4[i], b = t4[i];
+        const float rx = a.x - b.x, ry = a.y - b.y, rz = a.z - b.z, rw = a.w - b.w;
+        acc += (fabsf(rx) + fabsf(ry)) + (fabsf(rz) + fabsf(rw));
+        d4[i] = make_float4(scale * (float)((rx > 0.f) - (rx < 0.f)), scale * (float)((ry > 0.f) - (ry < 0.f)),
+                            scale * (float)((rz > 0.f) - (rz < 0.f)), scale * (float)((rw > 0.f) - (rw < 0.f)));
+    }
+    for (size_t i = 4 * n4 + blockIdx.x * (size_t)kRedThreads + threadIdx.x; i < total; i += stride) {
+        const float r = rgb[i] - tgt[i];
         acc += fabsf(r);
         dLdC[i] = scale * (float)((r > 0.f) - (r < 0.f));
     }
@@ -64,25 +78,72 @@ __global__ void __launch_bounds__(32) k_loss_final(const float* __restrict__ par
     }
 }
 
+// Fixed-order final reduction from two partial arrays.
+__global__ void __launch_bounds__(32) k_loss_final2(const float* __restrict__ photo, int n_photo,
+                                                    const float* __restrict__ reg, int n_reg, float* __restrict__ out) {
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n_photo; i += 32) a += photo[i];
+    for (int i = threadIdx.x; i < n_reg; i += 32) b += reg[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+        b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+    }
+    if (threadIdx.x == 0) {
+        out[0] = (float)(a + b);
+        out[1] = (float)a;
+        out[2] = (float)b;
+    }
+}
+
 struct AdamArgs {
     float lr[kParamRows];
-    float b1, b2, eps, bc1, bc2;
+    float b1, b2, eps;
 };
 
+// Bias corrections of the next Adam step, from the device-side step counter
+// (so that a captured graph replays correctly): st[4] = completed steps,
+// st[1] = pair-buffer overflow flag of this iteration (step skipped),
+// bc = {1 - beta1^t, 1 - beta2^t, skip}.
+__global__ void k_adam_prep(uint32_t* __restrict__ st, float b1, float b2, float* __restrict__ bc) {
+    const bool skip = st[1] != 0u;
+    const double t = (double)st[4] + 1.0;
+    bc[0] = (float)(1.0 - pow((double)b1, t));
+    bc[1] = (float)(1.0 - pow((double)b2, t));
+    bc[2] = skip ? 1.f : 0.f;
+    if (!skip) st[4] += 1u;
+}
+
+// One Adam step; each thread updates 4 consecutive parameters of one row.
 __global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, const float* __restrict__ G,
                                               float* __restrict__ M, float* __restrict__ V, int n, int cap,
-                                              AdamArgs a) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int row = blockIdx.y;
-    if (i >= n) return;
-    size_t k = (size_t)row * cap + i;
-    float g = G[k];
-    float m = a.b1 * M[k] + (1.f - a.b1) * g;
-    float v = a.b2 * V[k] + (1.f - a.b2) * g * g;
-    M[k] = m;
-    V[k] = v;
-    float mh = m / a.bc1, vh = v / a.bc2;
-    P[k] -= a.lr[row] * mh / (sqrtf(vh) + a.eps);
+                                              AdamArgs a, const float* __restrict__ bc) {
+    const int j = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int row = blockIdx.y;
+    if (j >= n || bc[2] != 0.f) return;
+    const float bc1 = bc[0], bc2 = bc[1], lr = a.lr[row];
+    const size_t k = (size_t)row * cap + j;
+    auto upd = [&](float& p, float g, float& m, float& v) {
+        m = a.b1 * m + (1.f - a.b1) * g;
+        v = a.b2 * v + (1.f - a.b2) * g * g;
+        const float mh = m / bc1, vh = v / bc2;
+        p -= lr * mh / (sqrtf(vh) + a.eps);
+    };
+    if (j + 3 < n) {
+        float4 p = *reinterpret_cast<float4*>(P + k);
+        const float4 g = *reinterpret_cast<const float4*>(G + k);
+        float4 m = *reinterpret_cast<float4*>(M + k);
+        float4 v = *reinterpret_cast<float4*>(V + k);
+        upd(p.x, g.x, m.x, v.x);
+        upd(p.y, g.y, m.y, v.y);
+        upd(p.z, g.z, m.z, v.z);
+        upd(p.w, g.w, m.w, v.w);
+        *reinterpret_cast<float4*>(P + k) = p;
+        *reinterpret_cast<float4*>(M + k) = m;
+        *reinterpret_cast<float4*>(V + k) = v;
+    } else {
+        for (int e = 0; e < 4 && j + e < n; ++e) upd(P[k + e], G[k + e], M[k + e], V[k + e]);
+    }
 }
 
 }  // namespace
@@ -101,6 +162,17 @@ cudaError_t launch_loss(gs_ctx* c, const DevConst& k, const float* rgb, const fl
     return cudaGetLastError();
 }
 
+cudaError_t launch_loss_tail(gs_ctx* c, const DevConst& k, const float* photo_partials, int n_photo,
+                             float* loss_out, cudaStream_t s) {
+    const int nb_reg = c->n_partials / 2;
+    float* reg_part = c->partials + c->n_partials / 2;
+    c->launches += 2;
+    k_planar<<<nb_reg, kRedThreads, 0, s>>>(c->params, c->n, c->cap, k.reg_floor,
+                                            c->n > 0 ? k.lambda_reg / (float)c->n : 0.f, reg_part);
+    k_loss_final2<<<1, 32, 0, s>>>(photo_partials, n_photo, reg_part, nb_reg, loss_out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_adam(gs_ctx* c, cudaStream_t s) {
     if (c->n == 0) return cudaSuccess;
     AdamArgs a;
@@ -109,13 +181,11 @@ cudaError_t launch_adam(gs_ctx* c, cudaStream_t s) {
     a.b1 = c->cfg.beta1;
     a.b2 = c->cfg.beta2;
     a.eps = c->cfg.eps;
-    // bias corrections of step t (computed in double on the host)
-    double t = (double)c->adam_t;
-    a.bc1 = (float)(1.0 - pow((double)c->cfg.beta1, t));
-    a.bc2 = (float)(1.0 - pow((double)c->cfg.beta2, t));
-    dim3 grid((c->n + 255) / 256, kParamRows);
-    ++c->launches;
-    k_adam<<<grid, 256, 0, s>>>(c->params, c->grads, c->adam_m, c->adam_v, c->n, c->cap, a);
+    float* bc = c->partials + c->n_partials + 4;
+    c->launches += 2;
+    k_adam_prep<<<1, 1, 0, s>>>(c->dcount, c->cfg.beta1, c->cfg.beta2, bc);
+    dim3 grid(((c->n + 3) / 4 + 255) / 256, kParamRows);
+    k_adam<<<grid, 256, 0, s>>>(c->params, c->grads, c->adam_m, c->adam_v, c->n, c->cap, a, bc);
     return cudaGetLastError();
 }
 
