@@ -52,6 +52,28 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+WINDOW_METRIC = "mapping window fwd+bwd iters/s @8x640x480,150k Gaussians"
+WINDOW_WORKLOAD = ("TUM-shaped keyframe window: 8 views 640x480, fx=fy=525, on a smooth path through the textured "
+                   "room, 150k Gaussians; one iteration = render all views + L1/planar loss + adjoint + one Adam step")
+
+
+def make_window_workload(seed: int = 0, n_views: int = 8, n_gauss: int = 150_000):
+    from synth import make_room, room_gaussians, room_trajectory
+    room = make_room(seed)
+    cams = room_trajectory(n_views, seed, 640, 480, 525.0, 525.0)
+    params = room_gaussians(room, n_gauss, seed)
+    cache = os.path.join(tempfile.gettempdir(), f"gs_room_window_{seed}_{n_views}.npy")
+    if os.path.exists(cache):
+        targets = np.load(cache)
+    else:
+        targets = np.stack([room.raycast(c) for c in cams])
+        try:
+            np.save(cache, targets)
+        except OSError:
+            pass
+    return params, cams, targets
+
+
 def make_workload(seed: int = 0):
     from synth import make_room, room_camera_single, room_gaussians
     room = make_room(seed)
@@ -308,7 +330,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": W, "height": H,
-                       "tile": gm.tile_size, "pixels_per_thread": args.ppt, "l2": "flushed between iterations (256 MB write)",
+                       "tile": gm.tile_size, "pixels_per_thread": gm.pixels_per_thread, "l2": "flushed between iterations (256 MB write)",
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(tgt.numel() * 4),
                     "d2h_bytes_per_step": 12},
@@ -332,13 +354,88 @@ def run_ours(args):
     return 0
 
 
+def run_window(args):
+    """Window workload: one call renders and back-propagates all 8 views (one persistent
+    compositing launch in the replayed graph) vs 8 single-view iterations, same GPU."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2504_02437_gb300 import build as B
+    B.build()
+    from paper_2504_02437_gb300.api import GaussianMap
+    params, cams, targets = make_window_workload(0)
+    dev = torch.device("cuda", 0)
+    V = len(cams)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    tgt = torch.as_tensor(targets, device=dev).contiguous()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+    gm = GaussianMap(capacity=params.shape[1], max_views=V, max_width=640, max_height=480, tile_size=args.tile,
+                     pixels_per_thread=args.ppt)
+    gm.set_params(torch.as_tensor(params, device=dev))
+    loss = torch.empty(3, device=dev)
+    gm.timing(True)
+    for _ in range(args.warmup):
+        gm.iterate(cams, tgt, loss)
+    gm.timing(True)
+    l0 = gm.launches
+    with ClockSampler(0) as clk:
+        ms_window = timed(lambda: gm.iterate(cams, tgt, loss), args.steps)
+    launches = gm.launches - l0
+    phases = gm.timing_read()
+    tile, ppt = gm.tile_size, gm.pixels_per_thread
+    visible = []
+    gm.render(cams)
+    for v in range(V):
+        visible.append(int((gm.debug_projection(v)[8] > 0).sum()))
+    gm.close()
+    # the same work as V single-view iterations (V Adam steps), one view per call
+    gs = GaussianMap(capacity=params.shape[1], max_views=1, max_width=640, max_height=480, tile_size=tile,
+                     pixels_per_thread=ppt)
+    gs.set_params(torch.as_tensor(params, device=dev))
+    singles = [tgt[v:v + 1].contiguous() for v in range(V)]
+    for _ in range(args.warmup):
+        for v in range(V):
+            gs.iterate(cams[v], singles[v], loss)
+
+    def seq():
+        for v in range(V):
+            gs.iterate(cams[v], singles[v], loss)
+    ms_seq = timed(seq, args.steps)
+    gs.close()
+    line = {"metric": WINDOW_METRIC, "value": 1000.0 / ms_window, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_window, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WINDOW_WORKLOAD, "n_gaussians": int(params.shape[1]), "views": V,
+                       "visible_per_view": visible, "tile": tile, "pixels_per_thread": ppt,
+                       "l2": "flushed between iterations (256 MB write)"},
+            "sequential": {"what": f"{V} single-view iterations (one per view, {V} Adam steps) per step",
+                           "ms_per_step": ms_seq, "speedup_of_window": ms_seq / ms_window},
+            "gpu_launches": int(launches),
+            "phases_ms": {k: round(v[0] / max(v[1], 1), 5) for k, v in phases.items()},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--tile", type=int, default=16, choices=[0, 8, 16])
+    ap.add_argument("--tile", type=int, default=0, choices=[0, 8, 16])
+    ap.add_argument("--workload", default="replica", choices=["replica", "window"])
     ap.add_argument("--ppt", type=int, default=0, choices=[0, 1, 2, 4])
     ap.add_argument("--cpu-tiles", type=int, default=160)
     ap.add_argument("--no-cpu", action="store_true")
@@ -347,6 +444,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "window":
+        return run_window(args)
     return run_ours(args)
 
 

@@ -159,11 +159,18 @@ GS_API int gs_backward(gs_ctx* ctx, const float* dL_drgb_dev, void* stream);
 /* One Adam step on every parameter with the gradient of the last gs_backward. */
 GS_API int gs_step(gs_ctx* ctx, void* stream);
 
-/* One full mapping iteration (Section 3.2 "Map Optimization"): render ->
- * loss -> backward -> Adam over the given views, recorded once per shape
- * into a CUDA graph and replayed. target_dev [n_views][3][H][W];
- * loss_dev optional float[3]; rgb_dev optional output image. Uses the
- * autotuned tile size when the config says 0. */
+/* One full mapping iteration (Section 3.2 "Map Optimization") over a window
+ * of n_views keyframes: projection, binning and sort for all views, then one
+ * persistent kernel that composites, takes the L1 gradient and runs the
+ * adjoint for every (view, tile), then the projection adjoint and Adam. The
+ * first call for a shape runs directly (and sizes the pair buffers); it is
+ * recorded into a CUDA graph that later calls replay with their cameras.
+ * target_dev [n_views][3][H][W]; loss_dev optional float[3]; rgb_dev optional
+ * output image. With tile_size 0 in the config, the first call for a new
+ * (image size, views, map-size bucket) first times the (tile size, pixels per
+ * thread) candidates without updating the map and keeps the fastest. An
+ * overflow of the pair buffer during a replay skips that iteration's Adam
+ * step; a later call then grows the buffer and returns GS_ERR_CAPACITY. */
 GS_API int gs_iterate(gs_ctx* ctx, const gs_camera* cams_host, int n_views, const float* target_dev,
                float* loss_dev, float* rgb_dev, void* stream);
 
@@ -249,6 +256,8 @@ GS_API int gs_debug_work(gs_ctx* ctx, int64_t* out_host);
 GS_API int64_t gs_launch_count(const gs_ctx* ctx);
 /* Tile size the last render used. */
 GS_API int gs_tile_size(const gs_ctx* ctx);
+/* Pixels per thread of the compositing kernels of the last render. */
+GS_API int gs_pixels_per_thread(const gs_ctx* ctx);
 
 #ifdef __cplusplus
 }

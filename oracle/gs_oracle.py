@@ -584,6 +584,38 @@ def plain_init(points, pixels, image, existing_means):
     return out
 
 
+def init_map(points, rgb):
+    """Eq. 6: one Gaussian per back-projected point with the plain initialisation, the
+    neighbours of each point being the other points. Returns params [14, n]."""
+    X = np.asarray(points, np.float64)
+    n = X.shape[0]
+    d2 = ((X[:, None, :] - X[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(d2, np.inf)
+    k = min(3, n - 1)
+    if k > 0:
+        rms = np.sqrt(np.sort(d2, axis=1)[:, :k].mean(1))
+    else:
+        rms = np.full(n, 0.01)
+    out = np.zeros((14, n))
+    out[0:3] = X.T
+    out[3:6] = np.clip(np.log(np.maximum(rms, 1e-30)), -7.0, -1.0)[None, :]
+    out[6] = 1.0
+    out[11:14] = np.asarray(rgb, np.float64).T
+    return out
+
+
+def screen_grad_norms(grad2d_views, valid_views):
+    """Per-Gaussian sum and count of |(dL/du, dL/dv)| over the views in which it is valid
+    (the statistic the densification reading thresholds)."""
+    s = np.zeros(len(valid_views[0]))
+    c = np.zeros(len(valid_views[0]))
+    for g, ok in zip(grad2d_views, valid_views):
+        nrm = np.sqrt(np.asarray(g["u"]) ** 2 + np.asarray(g["v"]) ** 2)
+        s += np.where(ok, nrm, 0.0)
+        c += np.asarray(ok, float)
+    return s, c
+
+
 # ------------------------------------------------------------------ densification split (gradient reading)
 
 

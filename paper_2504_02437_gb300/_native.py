@@ -64,6 +64,7 @@ SIGNATURES = {
     "gs_debug_pairs": (_I, [_P, _P, _P, C.c_int64, C.POINTER(C.c_int64)]),
     "gs_debug_grad2d": (_I, [_P, _P]),
     "gs_tile_size": (_I, [_P]),
+    "gs_pixels_per_thread": (_I, [_P]),
     "gs_timing_enable": (_I, [_P, _I]),
     "gs_timing_read": (_I, [_P, _P, _P]),
     "gs_debug_work": (_I, [_P, _P]),

@@ -106,6 +106,10 @@ class GaussianMap:
     def tile_size(self) -> int:
         return self.lib.gs_tile_size(self.ctx)
 
+    @property
+    def pixels_per_thread(self) -> int:
+        return self.lib.gs_pixels_per_thread(self.ctx)
+
     def set_params(self, params: torch.Tensor):
         p = params.detach().to(device=f"cuda:{self.device}", dtype=torch.float32).contiguous()
         if p.dim() != 2 or p.shape[0] != 14:

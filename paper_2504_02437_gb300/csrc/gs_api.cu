@@ -131,13 +131,28 @@ void drop_graph(gs_ctx* c) {
     c->cam_node = nullptr;
 }
 
-int pick_tile(gs_ctx* c, int w, int h) {
-    if (c->cfg.tile_size == 8 || c->cfg.tile_size == 16) return c->cfg.tile_size;
-    for (int i = 0; i < 4; ++i)
-        if (c->tuned_tile[i] && c->tuned_key[i][0] == w && c->tuned_key[i][1] == h &&
-            c->tuned_key[i][2] == ceil_log2((uint32_t)std::max(c->n, 1)))
-            return c->tuned_tile[i];
-    return 16;
+const gs_ctx::Tuned* find_tuned(const gs_ctx* c, int w, int h, int views) {
+    const int nb = ceil_log2((uint32_t)std::max(c->n, 1));
+    for (const auto& t : c->tuned)
+        if (t.w == w && t.h == h && t.views == views && t.nb == nb) return &t;
+    return nullptr;
+}
+
+// Tile size and pixels per thread of a render: the autotuner's candidate while
+// it times one, else the configured values, else the tuned choice, else 16 / 1.
+void pick_layout(gs_ctx* c, int w, int h, int views, int& tile, int& ppt) {
+    if (c->force_tile) {
+        tile = c->force_tile;
+        ppt = c->force_ppt;
+        return;
+    }
+    const gs_ctx::Tuned* t = c->cfg.tile_size == 0 ? find_tuned(c, w, h, views) : nullptr;
+    tile = c->cfg.tile_size == 8 || c->cfg.tile_size == 16 ? c->cfg.tile_size : (t ? t->tile : 16);
+    const int want = c->cfg.pixels_per_thread;
+    if (want == 1 || want == 2 || (want == 4 && tile == 16))
+        ppt = want;
+    else
+        ppt = (t && t->tile == tile) ? t->ppt : 1;
 }
 
 // Set up the per-view cameras of a render and upload them with a kernel (no
@@ -150,7 +165,8 @@ int prepare_views(gs_ctx* c, const gs_camera* cams, int n_views, CamBatch& b) {
         if (cams[v].width != cams[0].width || cams[v].height != cams[0].height)
             return fail(c, GS_ERR_ARG, "all views of one call must share one image size");
     }
-    int tile = pick_tile(c, cams[0].width, cams[0].height);
+    int tile = 16, ppt = 1;
+    pick_layout(c, cams[0].width, cams[0].height, n_views, tile, ppt);
     memset(&b, 0, sizeof(b));
     b.n = n_views;
     for (int v = 0; v < n_views; ++v) make_cam(cams[v], c->cfg, tile, v, b.cam[v]);
@@ -161,8 +177,7 @@ int prepare_views(gs_ctx* c, const gs_camera* cams, int n_views, CamBatch& b) {
     c->width = cams[0].width;
     c->height = cams[0].height;
     c->n_bins = bins;
-    const int want = c->cfg.pixels_per_thread;
-    c->ppt = (want == 1 || want == 2 || (want == 4 && tile == 16)) ? want : 1;
+    c->ppt = ppt;
     memcpy(c->hcam, b.cam, sizeof(DevCamera) * n_views);
     return GS_OK;
 }
@@ -404,6 +419,8 @@ int gs_num_gaussians(const gs_ctx* c) { return c ? c->n : 0; }
 
 int gs_tile_size(const gs_ctx* c) { return c ? c->tile : 0; }
 
+int gs_pixels_per_thread(const gs_ctx* c) { return c ? c->ppt : 0; }
+
 int64_t gs_launch_count(const gs_ctx* c) { return c ? c->launches : 0; }
 
 int gs_set_params(gs_ctx* c, const float* params_dev, int n, void* stream) {
@@ -527,6 +544,49 @@ int gs_step(gs_ctx* c, void* stream) {
     return GS_OK;
 }
 
+// The autotuner: times render + loss + adjoint (no Adam step, so the map is
+// unchanged) for each (tile size, pixels per thread) candidate on the caller's
+// views and keeps the fastest for this (image size, views, N-bucket).
+static int autotune(gs_ctx* c, const gs_camera* cams, int n_views, const float* target, float* rgb,
+                    cudaStream_t s) {
+    static const int cand[][2] = {{16, 1}, {16, 2}, {16, 4}, {8, 1}, {8, 2}};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const bool timing = c->timing;
+    c->timing = false;
+    float best = 1e30f;
+    int bt = 16, bp = 1, code = GS_OK;
+    for (const auto& cd : cand) {
+        c->force_tile = cd[0];
+        c->force_ppt = cd[1];
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && code == GS_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            code = gs_render(c, cams, n_views, rgb, nullptr, nullptr, s);
+            if (code == GS_OK) code = gs_loss(c, target, nullptr, s);
+            if (code == GS_OK) code = gs_backward(c, nullptr, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) code = GS_ERR_CUDA;
+            if (rep == 1) cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (code != GS_OK) break;
+        if (ms < best) {
+            best = ms;
+            bt = cd[0];
+            bp = cd[1];
+        }
+    }
+    c->force_tile = c->force_ppt = 0;
+    c->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (code != GS_OK) return code;
+    c->tuned.push_back({cams[0].width, cams[0].height, n_views, ceil_log2((uint32_t)std::max(c->n, 1)), bt, bp});
+    c->backward_ready = false;
+    return GS_OK;
+}
+
 int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* target, float* loss_dev, float* rgb,
                void* stream) {
     if (!c) return GS_ERR_ARG;
@@ -547,6 +607,12 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
         rgb = c->own_rgb;
     }
     float* loss_out = loss_dev ? loss_dev : c->partials + c->n_partials;
+    if (c->cfg.tile_size == 0 && c->n > 0 && !find_tuned(c, cams[0].width, cams[0].height, n_views)) {
+        if (n_views < 1 || n_views > c->cfg.max_views) return fail(c, GS_ERR_ARG, "bad views");
+        drop_graph(c);
+        int code = autotune(c, cams, n_views, target, rgb, s);
+        if (code != GS_OK) return code;
+    }
     // The flags of an earlier replay: a pair-buffer overflow there skipped its Adam step.
     if (c->graph && c->graph_pending && cudaEventQuery(c->graph_done) == cudaSuccess) {
         c->graph_pending = false;

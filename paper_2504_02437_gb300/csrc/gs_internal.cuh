@@ -150,9 +150,12 @@ struct gs_ctx {
     };
     std::vector<TimingRec> trec;
     std::vector<cudaEvent_t> tpool;
-    // autotuned tile size per (width, height, N-bucket)
-    int tuned_tile[4] = {0, 0, 0, 0};
-    int tuned_key[4][3];
+    // autotuned (tile size, pixels per thread) per (width, height, views, N-bucket)
+    struct Tuned {
+        int w, h, views, nb, tile, ppt;
+    };
+    std::vector<Tuned> tuned;
+    int force_tile = 0, force_ppt = 0;      // set while the autotuner times a candidate
 };
 
 namespace gs {

@@ -297,3 +297,19 @@ def test_iterate_graph_matches_plain_steps(scene):
     assert np.median(d) < 1e-7
     assert (d > 1e-5).mean() < 1e-3
     assert d.max() <= 2 * 5e-2 * len(cams)
+
+
+def test_autotuned_iterate_matches_fixed_layout(scene):
+    """With tile_size 0 the first iterate times the (tile, pixels-per-thread) candidates without
+    touching the map; the chosen layout gives the same iteration as a fixed one."""
+    p, cam, tg = scene
+    tgt = cuda(tg)
+    ga, gb = new_map(p.shape[1], tile_size=0), new_map(p.shape[1], tile_size=16, pixels_per_thread=1)
+    ga.set_params(cuda(p))
+    gb.set_params(cuda(p))
+    la = ga.iterate(cam, tgt).cpu().numpy()
+    lb = gb.iterate(cam, tgt).cpu().numpy()
+    assert ga.tile_size in (8, 16) and ga.pixels_per_thread in (1, 2, 4)
+    np.testing.assert_allclose(la, lb, rtol=1e-6)
+    d = np.abs(ga.params().cpu().numpy() - gb.params().cpu().numpy())
+    assert np.median(d) < 1e-7 and (d > 1e-5).mean() < 1e-3

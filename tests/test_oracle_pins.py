@@ -489,3 +489,20 @@ def test_split_threshold_and_order():
     assert mask.tolist() == [True, False, True, False]
     np.testing.assert_array_equal(newP[0:3, :2], P[0:3, [1, 3]])      # survivors first, in order
     np.testing.assert_array_equal(newP[0:3, 2:], P[0:3, [0, 0, 2, 2]])  # then children, z = 0
+
+
+def test_init_map_knn_excludes_self():
+    X = np.array([[0, 0, 0], [0.1, 0, 0], [0, 0.2, 0], [0, 0, 0.3], [5, 5, 5.0]])
+    out = O.init_map(X, np.full((5, 3), 0.5))
+    d = np.array([0.1, 0.2, 0.3])                      # nearest three of point 0: itself excluded
+    np.testing.assert_allclose(out[3, 0], math.log(math.sqrt((d ** 2).mean())), rtol=1e-12)
+    assert out[3, 4] == -1.0                           # far from all others: clamped
+    single = O.init_map(X[:1], np.zeros((1, 3)))
+    np.testing.assert_allclose(single[3:6, 0], math.log(0.01))
+
+
+def test_screen_grad_norms():
+    g = [{"u": np.array([3.0, 0.0]), "v": np.array([4.0, 1.0])}, {"u": np.array([0.0, 6.0]), "v": np.array([0.0, 8.0])}]
+    s, c = O.screen_grad_norms(g, [np.array([True, True]), np.array([False, True])])
+    np.testing.assert_allclose(s, [5.0, 11.0])
+    np.testing.assert_allclose(c, [1, 2])
