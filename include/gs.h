@@ -180,10 +180,50 @@ GS_API int gs_iterate(gs_ctx* ctx, const gs_camera* cams_host, int n_views, cons
  * front of the camera to a pixel whose opacity 1 - T exceeds insert_opacity
  * is skipped; every other point is appended with the plain initialisation
  * (log-scale from the 3 nearest existing means, colour of image_dev
- * [3][H][W] at the point's pixel). Writes the number appended to
- * *n_inserted_host. Synchronises the stream. */
+ * [3][H][W] at the point's pixel), or the learned initialiser when one is
+ * set (gs_set_initializer). Writes the number appended to *n_inserted_host
+ * and, when inserted_dev is not NULL, 1 or 0 per point to inserted_dev [n].
+ * Synchronises the stream. */
 GS_API int gs_insert(gs_ctx* ctx, const gs_camera* cam_host, const float* image_dev, const float* points_dev,
-              int n, int* n_inserted_host, void* stream);
+                     int n, int* n_inserted_host, uint8_t* inserted_dev, void* stream);
+
+/* ---- learned initialiser (the BF16 MLP of the learned-initialisation reading) ----
+ * A 3-layer MLP 80 -> 128 -> 128 -> 16 (GELU; the first 11 outputs are used)
+ * run on the tensor cores in BF16 with FP32 accumulation. Input per VO point:
+ * the keyframe's 5x5 RGB patch around the point's nearest pixel (borders
+ * clamped, row-major, RGB interleaved), its depth, its camera-frame position
+ * and a zero (80 floats). Output: log-scale (3), quaternion (4), opacity
+ * logit (1), colour (3). Parameters are float32, one flat array of
+ * gs_mlp_num_params() values: W1 [128][80], b1 [128], W2 [128][128], b2 [128],
+ * W3 [16][128], b3 [16] (rows 11..15 of W3 and b3 stay zero). */
+typedef struct gs_mlp gs_mlp;
+/* Create an MLP on `device` with uniform(+-1/sqrt(fan_in)) weights drawn from
+ * SplitMix64(seed) and zero biases. */
+GS_API int gs_mlp_create(int device, uint64_t seed, gs_mlp** out);
+GS_API void gs_mlp_destroy(gs_mlp* mlp);
+GS_API int gs_mlp_num_params(void);
+/* Copy parameters in (resets the Adam state) / out; flat_dev device float[gs_mlp_num_params()]. */
+GS_API int gs_mlp_set_params(gs_mlp* mlp, const float* flat_dev, void* stream);
+GS_API int gs_mlp_get_params(gs_mlp* mlp, float* flat_dev, void* stream);
+/* Gradient of the last gs_mlp_backward (same layout). */
+GS_API int gs_mlp_get_grads(gs_mlp* mlp, float* flat_dev, void* stream);
+/* Input features of n points (points_dev [n][3] world xyz) seen by cam in image_dev
+ * [3][H][W]: feat_dev [n][80]. */
+GS_API int gs_mlp_features(const gs_camera* cam_host, const float* image_dev, const float* points_dev, int n,
+                           float* feat_dev, void* stream);
+/* Predictions out_dev [n][16] of feat_dev [n][80]. */
+GS_API int gs_mlp_forward(gs_mlp* mlp, const float* feat_dev, int n, float* out_dev, void* stream);
+/* Mean-squared error over the 11 outputs against target_dev [n][16] (loss_dev optional
+ * float[1]) and its gradient w.r.t. all parameters (kept for gs_mlp_step). */
+GS_API int gs_mlp_backward(gs_mlp* mlp, const float* feat_dev, const float* target_dev, int n, float* loss_dev,
+                           void* stream);
+/* One Adam step (beta 0.9, 0.999, eps 1e-8) with learning rate lr. */
+GS_API int gs_mlp_step(gs_mlp* mlp, float lr, void* stream);
+/* Make gs_insert initialise new Gaussians with `mlp` (NULL restores the plain
+ * initialisation). A point whose prediction is non-finite, has a log-scale
+ * outside [-9, 1] or a zero quaternion keeps the plain initialisation. The
+ * context does not own the MLP. */
+GS_API int gs_set_initializer(gs_ctx* ctx, gs_mlp* mlp);
 
 /* Densification by splitting (reading of Section 3.2 "Clarity-Enhancing
  * Gaussian Densification" with the 3DGS gradient criterion the paper builds

@@ -651,3 +651,97 @@ def split(params, m, v, grad_sum, grad_cnt, normals, cfg: Config = Config()):
     newm = np.concatenate([np.asarray(m, np.float64)[:, keep], zeros], axis=1)
     newv = np.concatenate([np.asarray(v, np.float64)[:, keep], zeros], axis=1)
     return newP, newm, newv, mask
+
+
+# ------------------------------------------------------------------ learned initialiser (MLP reading)
+
+MLP_IN, MLP_HID, MLP_OUT, MLP_OUT_PAD = 80, 128, 11, 16
+# flat parameter layout: W1 [128][80], b1 [128], W2 [128][128], b2 [128], W3 [16][128], b3 [16]
+MLP_SHAPES = ((MLP_HID, MLP_IN), (MLP_HID,), (MLP_HID, MLP_HID), (MLP_HID,), (MLP_OUT_PAD, MLP_HID), (MLP_OUT_PAD,))
+MLP_SIZE = sum(int(np.prod(s)) for s in MLP_SHAPES)
+
+
+def bf16_round(x):
+    """Round float values to bfloat16 (round to nearest even), returned as float64."""
+    t = torch.as_tensor(np.asarray(x, np.float32))
+    return t.to(torch.bfloat16).to(torch.float64)
+
+
+def mlp_unflatten(flat):
+    flat = torch.as_tensor(flat)
+    out, o = [], 0
+    for s in MLP_SHAPES:
+        k = int(np.prod(s))
+        out.append(flat[o:o + k].reshape(s))
+        o += k
+    return out
+
+
+def gelu(x):
+    """GELU, erf form: x Phi(x)."""
+    return 0.5 * x * (1.0 + torch.erf(x / math.sqrt(2.0)))
+
+
+def mlp_features(points, cam, image):
+    """Input of the learned initialiser for each new point: the 5x5 RGB patch around the
+    point's nearest pixel (borders clamped; row-major, RGB interleaved), the depth, and the
+    point in camera coordinates, then one zero: [n, 80]."""
+    X = np.asarray(points, np.float64)
+    t = X @ np.asarray(cam.R, np.float64).T + np.asarray(cam.t, np.float64)
+    z = np.where(t[:, 2] > 1e-6, t[:, 2], 1e-6)
+    u = cam.fx * t[:, 0] / z + cam.cx
+    v = cam.fy * t[:, 1] / z + cam.cy
+    px = np.clip(np.floor(u + 0.5), 0, cam.width - 1).astype(np.int64)
+    py = np.clip(np.floor(v + 0.5), 0, cam.height - 1).astype(np.int64)
+    img = np.asarray(image, np.float64)
+    f = np.zeros((X.shape[0], MLP_IN))
+    k = 0
+    for dy in range(-2, 3):
+        for dx in range(-2, 3):
+            xx = np.clip(px + dx, 0, cam.width - 1)
+            yy = np.clip(py + dy, 0, cam.height - 1)
+            f[:, k:k + 3] = img[:, yy, xx].T
+            k += 3
+    f[:, 75] = t[:, 2]
+    f[:, 76:79] = t
+    return f
+
+
+def mlp_forward(flat, feats, round_bf16: bool = True):
+    """Forward pass: Y = W3 g(W2 g(W1 x + b1) + b2) + b3 with g = GELU. With ``round_bf16`` the
+    inputs, weights and hidden activations are rounded to bfloat16 (the tensor-core operands)
+    and everything else is float64. Returns Y [n, 16] (columns 11..15 are padding)."""
+    W1, b1, W2, b2, W3, b3 = [w.to(DT) for w in mlp_unflatten(torch.as_tensor(np.asarray(flat, np.float64)))]
+    r = bf16_round if round_bf16 else (lambda a: torch.as_tensor(np.asarray(a, np.float64)))
+    x = r(feats)
+    h1 = gelu(x @ r(W1.numpy()).T + b1)
+    h1 = r(h1.numpy()) if round_bf16 else h1
+    h2 = gelu(h1 @ r(W2.numpy()).T + b2)
+    h2 = r(h2.numpy()) if round_bf16 else h2
+    return (h2 @ r(W3.numpy()).T + b3).numpy()
+
+
+def mlp_loss_and_grad(flat, feats, targets, round_bf16: bool = True):
+    """Mean-squared error over the 11 outputs, (1 / (n 11)) sum (Y - T)^2, and its gradient
+    w.r.t. the flat float32 master parameters. The bfloat16 roundings of the forward are
+    treated as the identity in the derivative (the weights' gradient is taken at the rounded
+    values). Rows 11..15 of W3 and b3 get zero gradient."""
+    p = torch.as_tensor(np.asarray(flat, np.float64)).clone()
+    W1, b1, W2, b2, W3, b3 = mlp_unflatten(p)
+    r = (lambda a: bf16_round(a.detach().numpy())) if round_bf16 else (lambda a: a.detach())
+    leaves = [t.clone().requires_grad_(True) for t in (W1, b1, W2, b2, W3, b3)]
+    W1l, b1l, W2l, b2l, W3l, b3l = leaves
+
+    def ste(a):  # rounded value, identity derivative
+        return a + (r(a) - a.detach()) if round_bf16 else a
+
+    x = r(torch.as_tensor(np.asarray(feats, np.float64)))
+    h1 = ste(gelu(x @ ste(W1l).T + b1l))
+    h2 = ste(gelu(h1 @ ste(W2l).T + b2l))
+    y = h2 @ ste(W3l).T + b3l
+    T = torch.as_tensor(np.asarray(targets, np.float64))
+    n = y.shape[0]
+    loss = ((y[:, :MLP_OUT] - T[:, :MLP_OUT]) ** 2).sum() / (n * MLP_OUT)
+    loss.backward()
+    g = torch.cat([l.grad.reshape(-1) for l in leaves]).numpy()
+    return float(loss), g

@@ -9,7 +9,7 @@ from .build import build as build_library  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("GaussianMap", "rasterize", "to_gs_camera", "default_config"):
+    if name in ("GaussianMap", "MLP", "rasterize", "to_gs_camera", "default_config"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

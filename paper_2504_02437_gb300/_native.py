@@ -58,7 +58,7 @@ SIGNATURES = {
     "gs_backward": (_I, [_P, _P, _P]),
     "gs_step": (_I, [_P, _P]),
     "gs_iterate": (_I, [_P, C.POINTER(gs_camera), _I, _P, _P, _P, _P]),
-    "gs_insert": (_I, [_P, C.POINTER(gs_camera), _P, _P, _I, C.POINTER(_I), _P]),
+    "gs_insert": (_I, [_P, C.POINTER(gs_camera), _P, _P, _I, C.POINTER(_I), _P, _P]),
     "gs_densify": (_I, [_P, _P, C.POINTER(_I), _P]),
     "gs_debug_projection": (_I, [_P, _I, _P]),
     "gs_debug_pairs": (_I, [_P, _P, _P, C.c_int64, C.POINTER(C.c_int64)]),
@@ -70,6 +70,17 @@ SIGNATURES = {
     "gs_debug_work": (_I, [_P, _P]),
     "gs_launch_count": (C.c_int64, [_P]),
     "gs_sort_pairs_static": (_I, [_P, _P, _P, _P, C.c_int64, _I, _P]),
+    "gs_mlp_create": (_I, [_I, C.c_uint64, C.POINTER(_P)]),
+    "gs_mlp_destroy": (None, [_P]),
+    "gs_mlp_num_params": (_I, []),
+    "gs_mlp_set_params": (_I, [_P, _P, _P]),
+    "gs_mlp_get_params": (_I, [_P, _P, _P]),
+    "gs_mlp_get_grads": (_I, [_P, _P, _P]),
+    "gs_mlp_features": (_I, [C.POINTER(gs_camera), _P, _P, _I, _P, _P]),
+    "gs_mlp_forward": (_I, [_P, _P, _I, _P, _P]),
+    "gs_mlp_backward": (_I, [_P, _P, _P, _I, _P, _P]),
+    "gs_mlp_step": (_I, [_P, C.c_float, _P]),
+    "gs_set_initializer": (_I, [_P, _P]),
 }
 PHASES = ("project", "bin", "raster_fwd", "loss", "raster_bwd", "project_bwd", "adam", "raster_fused")
 

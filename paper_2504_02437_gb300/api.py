@@ -170,13 +170,22 @@ class GaussianMap:
         return loss_out
 
     # ---- map management
-    def insert(self, cam, image: torch.Tensor, points: torch.Tensor) -> int:
+    def insert(self, cam, image: torch.Tensor, points: torch.Tensor, return_mask: bool = False):
+        """Insert the points that are not behind rendered opacity > 0.99; returns the count
+        (and the per-point inserted mask with ``return_mask``)."""
         arr, V, H, W = _cams([cam])
         pts = points.to(torch.float32).contiguous()
         img = image.to(torch.float32).contiguous()
         n = C.c_int()
-        self._check(self.lib.gs_insert(self.ctx, arr, _ptr(img), _ptr(pts), pts.shape[0], C.byref(n), _stream()))
-        return n.value
+        mask = torch.empty(pts.shape[0], dtype=torch.uint8, device=pts.device) if return_mask else None
+        self._check(self.lib.gs_insert(self.ctx, arr, _ptr(img), _ptr(pts), pts.shape[0], C.byref(n), _ptr(mask),
+                                       _stream()))
+        return (n.value, mask.bool()) if return_mask else n.value
+
+    def set_initializer(self, mlp):
+        """Use the learned initialiser for insertions (None: the plain initialisation)."""
+        self._init_mlp = mlp
+        self._check(self.lib.gs_set_initializer(self.ctx, mlp.handle if mlp is not None else None))
 
     def densify(self, normals: Optional[torch.Tensor] = None) -> int:
         nz = None if normals is None else normals.to(torch.float32).contiguous()
@@ -220,6 +229,73 @@ class GaussianMap:
         out = np.empty((self._last_views, 9, self.n), np.float32)
         self._check(self.lib.gs_debug_grad2d(self.ctx, out.ctypes.data_as(C.c_void_p)))
         return out
+
+
+class MLP:
+    """The learned initialiser (BF16 tensor-core MLP) behind the C ABI."""
+
+    def __init__(self, seed: int = 0, device: int = 0):
+        self.lib = N.load()
+        self.device = device
+        h = C.c_void_p()
+        with torch.cuda.device(device):
+            N.check(self.lib.gs_mlp_create(device, seed, C.byref(h)))
+        self.handle = h
+        self.n_params = self.lib.gs_mlp_num_params()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.gs_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self):
+        return f"cuda:{self.device}"
+
+    def set_params(self, flat: torch.Tensor):
+        f = flat.to(device=self._dev(), dtype=torch.float32).contiguous()
+        N.check(self.lib.gs_mlp_set_params(self.handle, _ptr(f), _stream()))
+
+    def params(self) -> torch.Tensor:
+        out = torch.empty(self.n_params, device=self._dev())
+        N.check(self.lib.gs_mlp_get_params(self.handle, _ptr(out), _stream()))
+        return out
+
+    def grads(self) -> torch.Tensor:
+        out = torch.empty(self.n_params, device=self._dev())
+        N.check(self.lib.gs_mlp_get_grads(self.handle, _ptr(out), _stream()))
+        return out
+
+    @staticmethod
+    def features(cam, image: torch.Tensor, points: torch.Tensor) -> torch.Tensor:
+        lib = N.load()
+        arr, V, H, W = _cams([cam])
+        pts = points.to(torch.float32).contiguous()
+        img = image.to(torch.float32).contiguous()
+        out = torch.empty(pts.shape[0], 80, device=pts.device)
+        N.check(lib.gs_mlp_features(arr, _ptr(img), _ptr(pts), pts.shape[0], _ptr(out), _stream()))
+        return out
+
+    def forward(self, feats: torch.Tensor) -> torch.Tensor:
+        f = feats.to(torch.float32).contiguous()
+        out = torch.empty(f.shape[0], 16, device=f.device)
+        N.check(self.lib.gs_mlp_forward(self.handle, _ptr(f), f.shape[0], _ptr(out), _stream()))
+        return out
+
+    def backward(self, feats: torch.Tensor, targets: torch.Tensor) -> torch.Tensor:
+        f = feats.to(torch.float32).contiguous()
+        t = targets.to(torch.float32).contiguous()
+        loss = torch.empty(1, device=f.device)
+        N.check(self.lib.gs_mlp_backward(self.handle, _ptr(f), _ptr(t), f.shape[0], _ptr(loss), _stream()))
+        return loss
+
+    def step(self, lr: float):
+        N.check(self.lib.gs_mlp_step(self.handle, float(lr), _stream()))
 
 
 class _Rasterize(torch.autograd.Function):

@@ -970,8 +970,19 @@ int gs_init_map(gs_ctx* c, const float* pts, const float* rgb, int n, void* stre
     return GS_OK;
 }
 
+__global__ void k_mask_u8(const uint32_t* __restrict__ keep, int n, uint8_t* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = keep[i] ? 1 : 0;
+}
+
+int gs_set_initializer(gs_ctx* c, gs_mlp* mlp) {
+    if (!c) return GS_ERR_ARG;
+    c->init_mlp = mlp;
+    return GS_OK;
+}
+
 int gs_insert(gs_ctx* c, const gs_camera* cam, const float* image, const float* pts, int n, int* n_ins,
-              void* stream) {
+              uint8_t* inserted_dev, void* stream) {
     if (!c || !n_ins) return GS_ERR_ARG;
     *n_ins = 0;
     if (n < 0 || (n > 0 && (!pts || !image || !cam))) return fail(c, GS_ERR_ARG, "bad insertion arguments");
@@ -980,15 +991,20 @@ int gs_insert(gs_ctx* c, const gs_camera* cam, const float* image, const float* 
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(c->device));
     Temp t;
-    float *img = nullptr, *stage = nullptr;
+    float *img = nullptr, *stage = nullptr, *feat = nullptr;
     uint32_t *keep = nullptr, *pos = nullptr;
     const size_t HW = (size_t)cam->width * cam->height;
     if (!t.get(&img, 3 * HW) || !t.get(&stage, kParamRows * (size_t)n) || !t.get(&keep, (size_t)n) ||
-        !t.get(&pos, (size_t)n))
+        !t.get(&pos, (size_t)n) || !t.get(&feat, 80 * (size_t)n))
         return fail(c, GS_ERR_OOM, "temporary buffers");
     int code = gs_render(c, cam, 1, img, nullptr, nullptr, stream);
     if (code != GS_OK) return code;
     CK(launch_insert_test(c, c->hcam[0], pts, n, image, keep, stage, s));
+    if (c->init_mlp) CK(mlp_initialise(c->init_mlp, c->hcam[0], image, pts, n, stage, feat, s));
+    if (inserted_dev) {
+        k_mask_u8<<<(n + 255) / 256, 256, 0, s>>>(keep, n, inserted_dev);
+        CK(cudaGetLastError());
+    }
     CK(scan_u32(c, keep, pos, (uint32_t)n, c->dcount + 5, s));
     CK(launch_append(c, stage, n, keep, pos, s));
     CK(cudaMemcpyAsync(c->hcount + 5, c->dcount + 5, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));

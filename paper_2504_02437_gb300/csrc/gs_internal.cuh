@@ -156,6 +156,7 @@ struct gs_ctx {
     };
     std::vector<Tuned> tuned;
     int force_tile = 0, force_ppt = 0;      // set while the autotuner times a candidate
+    gs_mlp* init_mlp = nullptr;             // learned initialiser of gs_insert (NULL = plain)
 };
 
 namespace gs {
@@ -186,6 +187,9 @@ cudaError_t launch_loss(gs_ctx* c, const DevConst& k, const float* rgb, const fl
                         cudaStream_t s);
 cudaError_t launch_adam(gs_ctx* c, cudaStream_t s);
 cudaError_t launch_copy_T(gs_ctx* c, float* T_out, cudaStream_t s);
+// learned initialiser (k_mlp.cu): overwrite the staged plain parameters of the points
+cudaError_t mlp_initialise(gs_mlp* M, const DevCamera& cam, const float* image, const float* pts, int n, float* stage,
+                           float* feat_tmp, cudaStream_t s);
 // map management (k_map.cu)
 cudaError_t launch_init_points(gs_ctx* c, const float* pts, const float* rgb, int n, const float* ref, int ref_stride,
                                int n_ref, int ref_is_self, float* out_params, int out_stride, cudaStream_t s);

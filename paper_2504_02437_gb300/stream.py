@@ -1,0 +1,133 @@
+"""The mapping stream (Section 3.2 "Mapping") over a sequence of keyframes.
+
+Per keyframe j: the first keyframe initialises the map from its points (Eq. 6);
+every later one inserts its points through the opacity gate (Eq. 7 reading);
+then `iters` mapping iterations (render, L1 + planar loss, adjoint, Adam) run
+over the window of the last `window` keyframes, and the map is densified by
+splitting (densification reading). Every step runs in the library's kernels;
+this module only sequences the calls and keeps statistics.
+
+Also: collection of (features, converged parameters) pairs of inserted
+Gaussians, training of the learned initialiser on them, and the
+time-to-PSNR comparison of learned against plain initialisation.
+"""
+from __future__ import annotations
+
+import math
+import time
+from typing import List, Optional, Sequence
+
+import torch
+
+from .api import MLP, GaussianMap
+
+PATCH_CENTRE = slice(36, 39)   # RGB of the centre pixel of the 5x5 patch in the MLP features
+
+
+def psnr(img: torch.Tensor, ref: torch.Tensor) -> torch.Tensor:
+    """10 log10(1 / MSE) of images in [0, 1] (device scalar)."""
+    mse = torch.mean((img - ref) ** 2)
+    return 10.0 * torch.log10(1.0 / torch.clamp(mse, min=1e-12))
+
+
+def canonical_targets(params: torch.Tensor) -> torch.Tensor:
+    """Learned-initialiser targets [n, 16] from Gaussian parameters [14, n]: log-scale, the
+    quaternion normalised with w >= 0, opacity logit, colour; columns 11..15 zero."""
+    p = params.T
+    q = p[:, 6:10]
+    q = q / torch.clamp(q.norm(dim=1, keepdim=True), min=1e-12)
+    q = torch.where(q[:, :1] < 0, -q, q)
+    out = torch.zeros(p.shape[0], 16, device=p.device)
+    out[:, 0:3] = p[:, 3:6]
+    out[:, 3:7] = q
+    out[:, 7] = p[:, 10]
+    out[:, 8:11] = p[:, 11:14]
+    return out
+
+
+def run_stream(gm: GaussianMap, cams: Sequence, targets: torch.Tensor, points: Sequence[torch.Tensor],
+               window: int = 8, iters: int = 100, insert: bool = True, densify: bool = True,
+               collect: bool = False, track_psnr: bool = False, mlp: Optional[MLP] = None) -> dict:
+    """Run the mapping stream. ``targets`` [F, 3, H, W] and each ``points[j]`` [k, 3] live on the
+    device. With ``mlp`` the learned initialiser initialises inserted Gaussians. Returns
+    statistics: Gaussians per keyframe, inserted per keyframe, the newest keyframe's PSNR
+    after each iteration (with ``track_psnr``), mapping time, and (with ``collect``) the
+    features and converged parameters of the inserted Gaussians."""
+    F = len(cams)
+    H, W = targets.shape[2], targets.shape[3]
+    dev = targets.device
+    gm.set_initializer(mlp)
+    loss = torch.empty(3, device=dev)
+    n_gauss, n_inserted, psnr_curves, xs, ys = [], [], [], [], []
+    t_map = 0.0
+    for j in range(F):
+        feats = MLP.features(cams[j], targets[j], points[j]) if (collect or j == 0) else None
+        n0 = gm.n
+        if j == 0 or not insert:
+            if j == 0:
+                gm.init_map(points[j], feats[:, PATCH_CENTRE].contiguous())
+                mask = torch.ones(points[j].shape[0], dtype=torch.bool, device=dev)
+            k = gm.n - n0
+        else:
+            k, mask = gm.insert(cams[j], targets[j], points[j], return_mask=True)
+        n_inserted.append(int(k))
+        views = list(range(max(0, j - window + 1), j + 1))
+        wc = [cams[v] for v in views]
+        wt = targets[views[0]:j + 1].contiguous()
+        rgb = torch.empty(len(views), 3, H, W, device=dev) if track_psnr else None
+        curve = torch.empty(iters, device=dev) if track_psnr else None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for it in range(iters):
+            gm.iterate(wc, wt, loss, rgb)
+            if track_psnr:
+                curve[it] = psnr(rgb[-1], targets[j])
+        torch.cuda.synchronize()
+        t_map += time.perf_counter() - t0
+        if track_psnr:
+            psnr_curves.append(curve.cpu())
+        if collect and k > 0:
+            xs.append(feats[mask])
+            ys.append(canonical_targets(gm.params()[:, n0:n0 + k]))
+        if densify:
+            gm.densify()
+        n_gauss.append(gm.n)
+    gm.set_initializer(None)
+    out = {"n_gauss": n_gauss, "n_inserted": n_inserted, "map_seconds": t_map,
+           "iterations": F * iters, "iters_per_s": F * iters / max(t_map, 1e-9)}
+    if track_psnr:
+        out["psnr"] = torch.stack(psnr_curves)
+    if collect:
+        out["features"] = torch.cat(xs) if xs else torch.empty(0, 80, device=dev)
+        out["targets"] = torch.cat(ys) if ys else torch.empty(0, 16, device=dev)
+    return out
+
+
+def train_mlp(mlp: MLP, X: torch.Tensor, Y: torch.Tensor, epochs: int = 200, batch: int = 4096, lr: float = 1e-3,
+              seed: int = 0) -> List[float]:
+    """Minibatch Adam on the MSE between predictions and converged parameters (all on the GPU
+    in the library's kernels). Returns the loss of each epoch's last batch."""
+    g = torch.Generator(device=X.device)
+    g.manual_seed(seed)
+    n = X.shape[0]
+    losses = []
+    for _ in range(epochs):
+        perm = torch.randperm(n, device=X.device, generator=g)
+        last = None
+        for s in range(0, n, batch):
+            idx = perm[s:s + batch]
+            if idx.numel() < 16:
+                continue
+            last = mlp.backward(X[idx].contiguous(), Y[idx].contiguous())
+            mlp.step(lr)
+        if last is not None:
+            losses.append(float(last))
+    return losses
+
+
+def iterations_to_reach(curves: torch.Tensor, goals: torch.Tensor) -> torch.Tensor:
+    """Per keyframe, the first iteration (1-based) whose PSNR reaches the goal (len + 1 if never)."""
+    reached = curves >= goals[:, None]
+    first = torch.where(reached.any(1), reached.float().argmax(1) + 1,
+                        torch.full((curves.shape[0],), curves.shape[1] + 1))
+    return first

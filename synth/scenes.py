@@ -150,6 +150,51 @@ class Room:
             out[s:s + chunk] = self._shade(c, d_world[s:s + chunk])
         return out.T.reshape(3, H, W).astype(np.float32)
 
+    def raycast_torch(self, cam: Camera, device="cuda", chunk: int = 65536):
+        """The same ray-cast as ``raycast`` evaluated with float32 torch ops on ``device``
+        (for long synthetic sequences); returns a [3, H, W] float32 tensor there."""
+        import torch
+        f = dict(dtype=torch.float32, device=device)
+        W, H = cam.width, cam.height
+        R = torch.tensor(np.asarray(cam.R, np.float64), **f)
+        c = torch.tensor(cam.center(), **f)
+        py, px = torch.meshgrid(torch.arange(H, **f), torch.arange(W, **f), indexing="ij")
+        d_cam = torch.stack([(px.reshape(-1) - cam.cx) / cam.fx, (py.reshape(-1) - cam.cy) / cam.fy,
+                             torch.ones(H * W, **f)], 1)
+        d_world = d_cam @ R
+        o = torch.tensor(self.origin, **f)
+        e1 = torch.tensor(self.e1, **f)
+        e2 = torch.tensor(self.e2, **f)
+        ext = torch.tensor(self.ext, **f)
+        n = torch.cross(e1, e2, dim=1)
+        num = ((o - c[None, :]) * n).sum(1)
+        base = torch.tensor(self.base, **f)
+        wave = torch.tensor(self.wave, **f)
+        chk = torch.tensor(self.checker, **f)
+        out = torch.zeros(H * W, 3, **f)
+        for s0 in range(0, H * W, chunk):
+            d = d_world[s0:s0 + chunk]
+            denom = d @ n.T
+            t = num[None, :] / denom
+            p_rel = c[None, None, :] + t[:, :, None] * d[:, None, :] - o[None, :, :]
+            a = (p_rel * e1[None]).sum(-1)
+            b = (p_rel * e2[None]).sum(-1)
+            ok = (t > 1e-6) & (a >= 0) & (a <= ext[None, :, 0]) & (b >= 0) & (b <= ext[None, :, 1]) & torch.isfinite(t)
+            t_ok = torch.where(ok, t, torch.full_like(t, float("inf")))
+            k = torch.argmin(t_ok, dim=1)
+            rows = torch.arange(d.shape[0], device=device)
+            hitm = torch.isfinite(t_ok[rows, k])
+            aa, bb = a[rows, k], b[rows, k]
+            w = wave[k]
+            sn = torch.sin(w[:, 1] * aa + w[:, 3]) * torch.sin(w[:, 2] * bb + w[:, 4])
+            per = chk[k, 1]
+            ck = torch.remainder(torch.floor(aa / per) + torch.floor(bb / per), 2.0) * 2.0 - 1.0
+            col = base[k] + (w[:, 0] * sn)[:, None] * torch.tensor([1.0, 0.8, 0.6], **f) \
+                + (chk[k, 0] * ck)[:, None] * torch.tensor([0.7, 1.0, 0.9], **f) \
+                + (w[:, 5] * torch.sin(2.3 * w[:, 1] * bb + w[:, 3]))[:, None] * torch.tensor([0.5, 0.3, 1.0], **f)
+            out[s0:s0 + chunk] = torch.where(hitm[:, None], torch.clamp(col, 0.0, 1.0), torch.zeros_like(col))
+        return out.T.reshape(3, H, W).contiguous()
+
     def hit(self, c: np.ndarray, d: np.ndarray):
         """Nearest hit of rays c + t d (t > 0): returns t [R], rect id [R] (-1 on miss), a, b."""
         n = np.cross(self.e1, self.e2)                       # [K, 3]

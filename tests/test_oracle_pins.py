@@ -506,3 +506,65 @@ def test_screen_grad_norms():
     s, c = O.screen_grad_norms(g, [np.array([True, True]), np.array([False, True])])
     np.testing.assert_allclose(s, [5.0, 11.0])
     np.testing.assert_allclose(c, [1, 2])
+
+
+# ------------------------------------------------------------------ learned initialiser
+
+
+def _mlp_params(seed):
+    rng = np.random.default_rng(seed)
+    flat = rng.normal(0, 0.15, size=O.MLP_SIZE)
+    W1, b1, W2, b2, W3, b3 = O.mlp_unflatten(torch.tensor(flat))
+    W3[11:] = 0
+    b3[11:] = 0
+    return torch.cat([t.reshape(-1) for t in (W1, b1, W2, b2, W3, b3)]).numpy()
+
+
+def test_gelu_closed_forms():
+    x = torch.tensor([0.0, 1.0, -1.0, 3.0], dtype=torch.float64, requires_grad=True)
+    y = O.gelu(x)
+    from scipy.stats import norm
+    np.testing.assert_allclose(y.detach().numpy(), x.detach().numpy() * norm.cdf(x.detach().numpy()), rtol=1e-14)
+    y[0].backward()
+    assert x.grad[0].item() == pytest.approx(0.5, abs=1e-15)   # GELU'(0) = 1/2
+
+
+def test_mlp_forward_matches_explicit_layers():
+    flat = _mlp_params(0)
+    X = np.random.default_rng(1).normal(size=(5, 80))
+    W1, b1, W2, b2, W3, b3 = [t.numpy() for t in O.mlp_unflatten(torch.tensor(flat))]
+    from scipy.special import erf
+    g = lambda z: 0.5 * z * (1 + erf(z / np.sqrt(2)))  # noqa: E731
+    ref = g(g(X @ W1.T + b1) @ W2.T + b2) @ W3.T + b3
+    np.testing.assert_allclose(O.mlp_forward(flat, X, round_bf16=False), ref, rtol=1e-12, atol=1e-14)
+
+
+def test_mlp_gradient_finite_differences():
+    flat = _mlp_params(2)
+    rng = np.random.default_rng(3)
+    X, Tg = rng.normal(size=(6, 80)), rng.normal(size=(6, 16))
+    L, g = O.mlp_loss_and_grad(flat, X, Tg, round_bf16=False)
+    idx = rng.choice(O.MLP_SIZE - 16 * 128 - 16, size=40, replace=False)     # weights of the real rows
+    idx = np.concatenate([idx, O.MLP_SIZE - 16 - 2048 + np.arange(0, 11 * 128, 97), [O.MLP_SIZE - 16, O.MLP_SIZE - 6]])
+    for i in idx:
+        h = 1e-6
+        pp, pm = flat.copy(), flat.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (O.mlp_loss_and_grad(pp, X, Tg, False)[0] - O.mlp_loss_and_grad(pm, X, Tg, False)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * abs(g[i]) + 1e-9, (i, fd, g[i])
+    assert np.all(g[-16 + 11:] == 0) and np.all(g[O.MLP_SIZE - 16 - 5 * 128:O.MLP_SIZE - 16] == 0)
+
+
+def test_mlp_features_layout():
+    cam = Camera(20, 10, 10.0, 10.0, 10.0, 5.0)
+    img = np.zeros((3, 10, 20))
+    img[0] = np.arange(20)[None, :]
+    img[1] = np.arange(10)[:, None]
+    f = O.mlp_features(np.array([[0.0, 0.0, 2.0], [-2.05, -1.0, 1.0]]), cam, img)
+    # point 0 projects to pixel (10, 5): patch x 8..12, y 3..7
+    np.testing.assert_allclose(f[0, 0:75:3].reshape(5, 5), np.tile(np.arange(8, 13), (5, 1)))
+    np.testing.assert_allclose(f[0, 1:75:3].reshape(5, 5), np.tile(np.arange(3, 8)[:, None], (1, 5)))
+    # point 1 projects to (-10.5 + 10 -> pixel 0 after clamping), y 5 - 10 = -5 -> 0: borders clamp
+    assert np.all(f[1, 0:75:3] >= 0) and f[1, 0] == 0 and f[1, 1] == 0
+    np.testing.assert_allclose(f[0, 75:80], [2.0, 0.0, 0.0, 2.0, 0.0])
