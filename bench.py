@@ -428,6 +428,143 @@ def run_window(args):
     return 0
 
 
+STREAM_METRIC = "mapping stream iters/s: 8-keyframe window x 100 iterations per keyframe, 640x480, insertion + densification"
+STREAM_WORKLOAD = ("mapping stream over a synthetic room sequence: {F} keyframes at 640x480 (fx=fy=525) on a smooth "
+                   "path, 96 VO-style points per keyframe (surface point + N(0, 0.01^2) per axis), opacity-gated "
+                   "insertion, {I} Adam iterations per keyframe over the last 8 keyframes, NDC-gradient split after each")
+TTP_METRIC = ("time-to-PSNR, learned vs plain initialisation: ms of mapping iterations until the newest keyframe "
+              "reaches the PSNR plain initialisation has after 100 iterations (held-out sequences)")
+
+
+def _stream_map(capacity, args):
+    from paper_2504_02437_gb300.api import GaussianMap
+    return GaussianMap(capacity=capacity, max_views=8, max_width=640, max_height=480, tile_size=args.tile,
+                       pixels_per_thread=args.ppt)
+
+
+def time_to_psnr(train_seeds, heldout_seeds, frames, iters, args, epochs=300, log=None):
+    """Learned-initialiser protocol: collect (features, converged parameters) pairs from plain
+    streams of ``train_seeds``, train the MLP with the library's kernels, then run each held-out
+    sequence twice (plain, learned) and compare per keyframe (keyframe 0 is initialised the
+    same way in both and is left out) the iterations and mapping ms until the newest keyframe's
+    PSNR reaches the plain run's PSNR after ``iters`` iterations."""
+    import torch
+    from synth import stream_sequence
+    from paper_2504_02437_gb300.api import MLP
+    from paper_2504_02437_gb300 import stream as S
+    t0 = time.perf_counter()
+    X, Y = [], []
+    for sd in train_seeds:
+        cams, tg, pts = stream_sequence(sd, frames)
+        gm = _stream_map(200_000, args)
+        st = S.run_stream(gm, cams, tg, pts, iters=iters, collect=True)
+        gm.close()
+        X.append(st["features"])
+        Y.append(st["targets"])
+    X, Y = torch.cat(X), torch.cat(Y)
+    t_collect = time.perf_counter() - t0
+    mlp = MLP(seed=0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    losses = S.train_mlp(mlp, X, Y, epochs=epochs, batch=4096, lr=1e-3)
+    ev[1].record()
+    torch.cuda.synchronize()
+    train_ms = ev[0].elapsed_time(ev[1])
+    it_plain, it_mlp, ms_plain, ms_mlp, p_plain, p_mlp, p1_plain, p1_mlp = [], [], [], [], [], [], [], []
+    reached = 0
+    for sd in heldout_seeds:
+        cams, tg, pts = stream_sequence(sd, frames)
+        runs = {}
+        for name, m in (("plain", None), ("mlp", mlp)):
+            gm = _stream_map(200_000, args)
+            runs[name] = S.run_stream(gm, cams, tg, pts, iters=iters, track_psnr="curve", mlp=m)
+            gm.close()
+        cp, cm = runs["plain"]["psnr"][1:], runs["mlp"]["psnr"][1:]
+        goal = cp[:, -1]
+        k_m = S.iterations_to_reach(cm, goal)
+        reached += int((k_m <= iters).sum())
+        k_m = torch.clamp(k_m, max=iters)
+        for j in range(cp.shape[0]):
+            itp = runs["plain"]["iteration_ms"][j + 1]
+            itm = runs["mlp"]["iteration_ms"][j + 1]
+            it_plain.append(iters)
+            it_mlp.append(int(k_m[j]))
+            ms_plain.append(sum(itp))
+            ms_mlp.append(sum(itm[:int(k_m[j])]))
+        p_plain += goal.tolist()
+        p_mlp += cm[:, -1].tolist()
+        p1_plain += cp[:, 0].tolist()
+        p1_mlp += cm[:, 0].tolist()
+    n = len(it_mlp)
+    return {"train_seeds": list(train_seeds), "heldout_seeds": list(heldout_seeds), "frames": frames,
+            "iterations_per_keyframe": iters, "training_pairs": int(X.shape[0]), "collect_s": round(t_collect, 2),
+            "train_epochs": epochs, "train_ms": round(train_ms, 1), "train_loss_first_last": [losses[0], losses[-1]],
+            "keyframes_compared": n, "mlp_reached_goal": reached,
+            "iterations_to_goal": {"plain": float(np.mean(it_plain)), "mlp_mean": float(np.mean(it_mlp)),
+                                   "mlp_median": float(np.median(it_mlp))},
+            "ms_to_goal": {"plain": float(np.sum(ms_plain)), "mlp": float(np.sum(ms_mlp))},
+            "speedup": float(np.sum(ms_plain) / max(np.sum(ms_mlp), 1e-9)),
+            "psnr_after_100": {"plain_mean": float(np.mean(p_plain)), "mlp_mean": float(np.mean(p_mlp))},
+            "psnr_after_1": {"plain_mean": float(np.mean(p1_plain)), "mlp_mean": float(np.mean(p1_mlp))}}
+
+
+def run_stream_bench(args):
+    """Config-4 stream: every keyframe inserts its VO points, runs 100 window iterations and
+    densifies; iterations are timed one by one with CUDA events, L2 flushed between them."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2504_02437_gb300 import build as B
+    B.build()
+    from synth import stream_sequence
+    from paper_2504_02437_gb300 import stream as S
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    F, I = args.frames, 100
+    # warm-up: a short stream of another sequence (builds, autotunes the small shapes)
+    cams, tg, pts = stream_sequence(1, args.warmup)
+    gm = _stream_map(200_000, args)
+    S.run_stream(gm, cams, tg, pts, iters=I)
+    gm.close()
+    cams, tg, pts = stream_sequence(0, F)
+    gm = _stream_map(200_000, args)
+    with ClockSampler(0) as clk:
+        st = S.run_stream(gm, cams, tg, pts, iters=I, track_psnr="final", flush=flush)
+    tile, ppt = gm.tile_size, gm.pixels_per_thread
+    gm.close()
+    ps = st["psnr"].tolist()
+    line = {"metric": STREAM_METRIC, "value": st["iters_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": st["iterations"], "warmup": args.warmup, "ms_per_step": 1000.0 / st["iters_per_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": STREAM_WORKLOAD.format(F=F, I=I), "frames": F, "window": 8,
+                       "iterations_per_keyframe": I, "tile": tile, "pixels_per_thread": ppt,
+                       "l2": "flushed between iterations (256 MB write)",
+                       "warmup": f"{args.warmup}-keyframe stream of another sequence"},
+            "n_gaussians_per_keyframe": st["n_gauss"], "inserted_per_keyframe": st["n_inserted"],
+            "psnr_newest_keyframe_after_100": [round(x, 3) for x in ps],
+            "psnr_mean_last_20": float(np.mean(ps[-20:])),
+            "map_s": st["map_seconds"], "insert_ms_total": st["insert_ms"], "densify_ms_total": st["densify_ms"],
+            "gpu_launches": int(st["launches"]), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ttp_bench(args):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2504_02437_gb300 import build as B
+    B.build()
+    with ClockSampler(0) as clk:
+        r = time_to_psnr(range(args.train_seeds), range(100, 100 + args.heldout_seeds), args.frames, 100, args)
+    line = {"metric": TTP_METRIC, "value": r["speedup"], "unit": "x (plain ms / learned ms to the same PSNR)",
+            "n_gpus": 1, "steps": r["keyframes_compared"], "warmup": 0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 MLP, f32 mapping", "data": "synthetic",
+            "config": {"workload": STREAM_WORKLOAD.format(F=args.frames, I=100) +
+                       "; MLP trained on the plain runs of the training seeds, compared on held-out seeds"},
+            "time_to_psnr": r, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -435,7 +572,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, default=0, choices=[0, 8, 16])
-    ap.add_argument("--workload", default="replica", choices=["replica", "window"])
+    ap.add_argument("--workload", default="replica", choices=["replica", "window", "stream", "learned_init"])
+    ap.add_argument("--frames", type=int, default=200)
+    ap.add_argument("--train-seeds", type=int, default=5)
+    ap.add_argument("--heldout-seeds", type=int, default=5)
     ap.add_argument("--ppt", type=int, default=0, choices=[0, 1, 2, 4])
     ap.add_argument("--cpu-tiles", type=int, default=160)
     ap.add_argument("--no-cpu", action="store_true")
@@ -446,6 +586,10 @@ def main():
         return run_reference(args)
     if args.workload == "window":
         return run_window(args)
+    if args.workload == "stream":
+        return run_stream_bench(args)
+    if args.workload == "learned_init":
+        return run_ttp_bench(args)
     return run_ours(args)
 
 

@@ -80,7 +80,7 @@ typedef struct gs_config {
     float beta1, beta2, eps;     /* Adam (0.9, 0.999, 1e-15)                          */
     float lr[5];         /* Adam learning rates: means, log-scales, quaternions,
                             opacity logits, colours (1e-3, 5e-3, 1e-3, 5e-2, 2.5e-3) */
-    float split_thresh;  /* split if mean screen-space grad norm > this (2e-4)        */
+    float split_thresh;  /* split if mean NDC position-grad norm > this (2e-4)        */
     float split_factor;  /* children log-scale -= ln(split_factor) (1.6)              */
     float insert_opacity;/* skip a new point if rendered opacity > this (0.99)        */
     int32_t tile_size;   /* 8 or 16 pixels; 0 = pick by the built-in autotuner        */
@@ -227,8 +227,9 @@ GS_API int gs_set_initializer(gs_ctx* ctx, gs_mlp* mlp);
 
 /* Densification by splitting (reading of Section 3.2 "Clarity-Enhancing
  * Gaussian Densification" with the 3DGS gradient criterion the paper builds
- * on): every Gaussian whose mean screen-space position-gradient norm over the
- * backward passes in which it was visible exceeds split_thresh is replaced by
+ * on): every Gaussian whose mean position-gradient norm in normalised device
+ * coordinates, |(dL/du W/2, dL/dv H/2)| with u, v in pixels, over the backward
+ * passes in which it was visible exceeds split_thresh is replaced by
  * two children with means mu + R S z (z standard normal), log-scales reduced
  * by ln(split_factor), other parameters copied and Adam moments zeroed. The
  * survivors keep their order; children follow in parent order.

@@ -604,13 +604,15 @@ def init_map(points, rgb):
     return out
 
 
-def screen_grad_norms(grad2d_views, valid_views):
-    """Per-Gaussian sum and count of |(dL/du, dL/dv)| over the views in which it is valid
-    (the statistic the densification reading thresholds)."""
+def screen_grad_norms(grad2d_views, valid_views, sizes):
+    """Per-Gaussian sum and count of the norm of the position gradient in normalised device
+    coordinates, |(dL/du * W/2, dL/dv * H/2)|, over the views in which it is valid (the statistic
+    the densification reading thresholds). ``sizes`` holds each view's (W, H): the pixel
+    coordinate u spans W pixels over the NDC interval [-1, 1], so du/dx_ndc = W/2."""
     s = np.zeros(len(valid_views[0]))
     c = np.zeros(len(valid_views[0]))
-    for g, ok in zip(grad2d_views, valid_views):
-        nrm = np.sqrt(np.asarray(g["u"]) ** 2 + np.asarray(g["v"]) ** 2)
+    for g, ok, (W, H) in zip(grad2d_views, valid_views, sizes):
+        nrm = np.sqrt((np.asarray(g["u"]) * (W / 2.0)) ** 2 + (np.asarray(g["v"]) * (H / 2.0)) ** 2)
         s += np.where(ok, nrm, 0.0)
         c += np.asarray(ok, float)
     return s, c
@@ -620,7 +622,7 @@ def screen_grad_norms(grad2d_views, valid_views):
 
 
 def split(params, m, v, grad_sum, grad_cnt, normals, cfg: Config = Config()):
-    """Split every Gaussian whose mean screen-space gradient norm exceeds ``split_thresh``.
+    """Split every Gaussian whose mean NDC position-gradient norm exceeds ``split_thresh``.
 
     mean = grad_sum / grad_cnt over the iterations in which it was visible (0 if never).
     Each split parent is replaced by two children with means mu + R S z_k (z_k the given

@@ -185,7 +185,10 @@ __global__ void __launch_bounds__(128) k_preprocess_backward(
         dr += g1.z;
         dg += g1.w;
         db += g8;
-        gsum += sqrtf(gu * gu + gv * gv);
+        {   // densification statistic: position-gradient norm in NDC (du/dx_ndc = W/2)
+            const float nu = gu * (0.5f * (float)cam.width), nv = gv * (0.5f * (float)cam.height);
+            gsum += sqrtf(nu * nu + nv * nv);
+        }
         gcnt += 1.f;
         project_one(p, g, cam, kc.dilation, o);
         // conic (a, b, c) = inverse of [[A, B], [B, C]]

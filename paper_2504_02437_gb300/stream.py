@@ -13,8 +13,6 @@ time-to-PSNR comparison of learned against plain initialisation.
 """
 from __future__ import annotations
 
-import math
-import time
 from typing import List, Optional, Sequence
 
 import torch
@@ -47,56 +45,93 @@ def canonical_targets(params: torch.Tensor) -> torch.Tensor:
 
 def run_stream(gm: GaussianMap, cams: Sequence, targets: torch.Tensor, points: Sequence[torch.Tensor],
                window: int = 8, iters: int = 100, insert: bool = True, densify: bool = True,
-               collect: bool = False, track_psnr: bool = False, mlp: Optional[MLP] = None) -> dict:
+               collect: bool = False, track_psnr: str = "", mlp: Optional[MLP] = None,
+               flush: Optional[torch.Tensor] = None) -> dict:
     """Run the mapping stream. ``targets`` [F, 3, H, W] and each ``points[j]`` [k, 3] live on the
-    device. With ``mlp`` the learned initialiser initialises inserted Gaussians. Returns
-    statistics: Gaussians per keyframe, inserted per keyframe, the newest keyframe's PSNR
-    after each iteration (with ``track_psnr``), mapping time, and (with ``collect``) the
-    features and converged parameters of the inserted Gaussians."""
+    device. With ``mlp`` the learned initialiser initialises inserted Gaussians.
+
+    ``track_psnr``: "" (none), "final" (the newest keyframe's PSNR after its last iteration,
+    computed outside the timed region) or "curve" (after every iteration). Mapping time is
+    taken with CUDA events around every iteration (PSNR kernels and the optional L2 ``flush``
+    write run between the brackets); insertion and densification are timed apart.
+
+    Returns statistics: Gaussians after each keyframe, inserted per keyframe, per-keyframe
+    mapping ms, insertion and densification ms, PSNR ("psnr": [F] or [F, iters]), and (with
+    ``collect``) the features of the inserted Gaussians with their parameters after the
+    keyframe's iterations (canonical form) as training pairs for the initialiser."""
     F = len(cams)
     H, W = targets.shape[2], targets.shape[3]
     dev = targets.device
+    stream = torch.cuda.current_stream(dev)
     gm.set_initializer(mlp)
     loss = torch.empty(3, device=dev)
-    n_gauss, n_inserted, psnr_curves, xs, ys = [], [], [], [], []
-    t_map = 0.0
-    for j in range(F):
-        feats = MLP.features(cams[j], targets[j], points[j]) if (collect or j == 0) else None
-        n0 = gm.n
-        if j == 0 or not insert:
+    n_gauss, n_inserted, xs, ys = [], [], [], []
+    ev_map, ev_ins, ev_den, curves, finals = [], [], [], [], []
+    launches0 = gm.launches
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+    try:
+        for j in range(F):
+            feats = MLP.features(cams[j], targets[j], points[j]) if (collect or j == 0) else None
+            n0 = gm.n
+            e0 = ev()
             if j == 0:
                 gm.init_map(points[j], feats[:, PATCH_CENTRE].contiguous())
                 mask = torch.ones(points[j].shape[0], dtype=torch.bool, device=dev)
-            k = gm.n - n0
-        else:
-            k, mask = gm.insert(cams[j], targets[j], points[j], return_mask=True)
-        n_inserted.append(int(k))
-        views = list(range(max(0, j - window + 1), j + 1))
-        wc = [cams[v] for v in views]
-        wt = targets[views[0]:j + 1].contiguous()
-        rgb = torch.empty(len(views), 3, H, W, device=dev) if track_psnr else None
-        curve = torch.empty(iters, device=dev) if track_psnr else None
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for it in range(iters):
-            gm.iterate(wc, wt, loss, rgb)
-            if track_psnr:
-                curve[it] = psnr(rgb[-1], targets[j])
-        torch.cuda.synchronize()
-        t_map += time.perf_counter() - t0
-        if track_psnr:
-            psnr_curves.append(curve.cpu())
-        if collect and k > 0:
-            xs.append(feats[mask])
-            ys.append(canonical_targets(gm.params()[:, n0:n0 + k]))
-        if densify:
-            gm.densify()
-        n_gauss.append(gm.n)
-    gm.set_initializer(None)
-    out = {"n_gauss": n_gauss, "n_inserted": n_inserted, "map_seconds": t_map,
-           "iterations": F * iters, "iters_per_s": F * iters / max(t_map, 1e-9)}
-    if track_psnr:
-        out["psnr"] = torch.stack(psnr_curves)
+                k = gm.n - n0
+            elif insert:
+                k, mask = gm.insert(cams[j], targets[j], points[j], return_mask=True)
+            else:
+                k, mask = 0, None
+            e1 = ev()
+            ev_ins.append((e0, e1))
+            n_inserted.append(int(k))
+            views = list(range(max(0, j - window + 1), j + 1))
+            wc = [cams[v] for v in views]
+            wt = targets[views[0]:j + 1]
+            rgb = torch.empty(len(views), 3, H, W, device=dev)
+            curve = torch.empty(iters, device=dev) if track_psnr == "curve" else None
+            its = []
+            for it in range(iters):
+                if flush is not None:
+                    flush.zero_()
+                a = ev()
+                gm.iterate(wc, wt, loss, rgb)
+                its.append((a, ev()))
+                if curve is not None:
+                    curve[it] = psnr(rgb[-1], targets[j])
+            ev_map.append(its)
+            if curve is not None:
+                curves.append(curve)
+            elif track_psnr == "final":
+                finals.append(psnr(rgb[-1], targets[j]))
+            if collect and k > 0:
+                xs.append(feats[mask])
+                ys.append(canonical_targets(gm.params()[:, n0:n0 + k]))
+            d0 = ev()
+            if densify:
+                gm.densify()
+            ev_den.append((d0, ev()))
+            n_gauss.append(gm.n)
+    finally:
+        gm.set_initializer(None)
+    torch.cuda.synchronize(dev)
+    it_ms = [[x.elapsed_time(y) for x, y in its] for its in ev_map]
+    kf_ms = [sum(m) for m in it_ms]
+    t_map = sum(kf_ms) / 1000.0
+    out = {"n_gauss": n_gauss, "n_inserted": n_inserted, "keyframe_ms": kf_ms, "iteration_ms": it_ms,
+           "map_seconds": t_map,
+           "insert_ms": sum(x.elapsed_time(y) for x, y in ev_ins),
+           "densify_ms": sum(x.elapsed_time(y) for x, y in ev_den),
+           "iterations": F * iters, "iters_per_s": F * iters / max(t_map, 1e-9),
+           "launches": gm.launches - launches0}
+    if track_psnr == "curve":
+        out["psnr"] = torch.stack(curves).cpu()
+    elif track_psnr == "final":
+        out["psnr"] = torch.stack(finals).cpu()
     if collect:
         out["features"] = torch.cat(xs) if xs else torch.empty(0, 80, device=dev)
         out["targets"] = torch.cat(ys) if ys else torch.empty(0, 16, device=dev)

@@ -17,4 +17,5 @@ from .scenes import (  # noqa: F401
     room_camera_single,
     room_trajectory,
     vo_points,
+    stream_sequence,
 )

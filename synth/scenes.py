@@ -202,9 +202,9 @@ class Room:
         num = np.einsum("kj,kj->k", self.origin - c[None, :], n)
         with np.errstate(divide="ignore", invalid="ignore"):
             t = num[None, :] / denom
-        p_rel = c[None, None, :] + t[:, :, None] * d[:, None, :] - self.origin[None, :, :]
-        a = np.einsum("rkj,kj->rk", p_rel, self.e1)
-        b = np.einsum("rkj,kj->rk", p_rel, self.e2)
+            p_rel = c[None, None, :] + t[:, :, None] * d[:, None, :] - self.origin[None, :, :]
+            a = np.einsum("rkj,kj->rk", p_rel, self.e1)
+            b = np.einsum("rkj,kj->rk", p_rel, self.e2)
         ok = (t > 1e-6) & (a >= 0) & (a <= self.ext[None, :, 0]) & (b >= 0) & (b <= self.ext[None, :, 1]) \
             & np.isfinite(t)
         t_ok = np.where(ok, t, np.inf)
@@ -364,3 +364,20 @@ def vo_points(room: Room, cam: Camera, n: int = 96, seed: int = 0, noise: float 
     t = np.where(np.isfinite(t), t, 1.0)
     pts = c[None, :] + t[:, None] * d_world + rng.normal(0.0, noise, size=(n, 3))
     return pts.astype(np.float32), np.stack([px, py], axis=1).astype(np.int32)
+
+
+def stream_sequence(seed: int, n_frames: int, width: int = 640, height: int = 480, fx: float = 525.0,
+                    n_points: int = 96, noise: float = 0.01, device="cuda"):
+    """A mapping-stream input: the room of ``seed``, ``n_frames`` keyframes on its smooth
+    trajectory, each keyframe's ray-cast image and its ``n_points`` VO-style points.
+
+    Returns (cameras, targets [F, 3, H, W] float32 on ``device``, [points [n, 3] float32 on
+    ``device``] per keyframe). The point draw of keyframe j is seeded by 1000 * seed + j.
+    """
+    import torch
+    room = make_room(seed)
+    cams = room_trajectory(n_frames, seed, width, height, fx, fx)
+    targets = torch.stack([room.raycast_torch(c, device) for c in cams])
+    pts = [torch.as_tensor(vo_points(room, c, n_points, 1000 * seed + j, noise)[0], device=device)
+           for j, c in enumerate(cams)]
+    return cams, targets, pts

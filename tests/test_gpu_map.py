@@ -2,7 +2,7 @@
 
 * gs_init_map: Eq. 6 map initialisation (plain initialisation, neighbours = the other new points);
 * gs_insert: the opacity-gated insertion reading of Eq. 7 with the plain initialisation;
-* gs_densify: the gradient-norm split of the densification reading, with given normal samples.
+* gs_densify: the NDC gradient-norm split of the densification reading, with given normal samples.
 Decisions taken in floating point (opacity > 0.99, mean gradient norm > threshold) are
 compared only where they lie well away from their thresholds; the rest is compared
 element by element.
@@ -100,7 +100,7 @@ def test_densify_matches_oracle():
     p64 = p.astype(np.float64)
     ref = O.loss_and_grads(p64, [cam], tg, want_2d=True)
     pr = O.project(torch.tensor(p64), cam)
-    s, c = O.screen_grad_norms(ref["grad2d"], [pr["valid"].numpy()])
+    s, c = O.screen_grad_norms(ref["grad2d"], [pr["valid"].numpy()], [(cam.width, cam.height)])
     mean = np.where(c > 0, s / np.maximum(c, 1), 0.0)
     # a threshold in a wide gap of the statistic, so float32 rounding cannot move a decision
     srt = np.sort(mean[mean > 0])

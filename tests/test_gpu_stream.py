@@ -1,0 +1,82 @@
+"""The mapping stream end to end on the GPU: insertion, window iterations and densification
+over a short synthetic keyframe sequence, and what the trained learned initialiser gains
+over plain initialisation on a held-out sequence (iterations to the same PSNR).
+
+The gain is empirical (the paper gives no value to match); the bound asserted here is a
+conservative floor under what the same protocol shows at full size.
+"""
+import numpy as np
+import pytest
+import torch
+
+from synth import stream_sequence
+
+pytestmark = pytest.mark.gpu
+
+W, H, FX = 320, 240, 262.5       # bookkeeping tests run at quarter size
+
+
+def _map(cap=1_000_000):
+    from paper_2504_02437_gb300.api import GaussianMap
+    return GaussianMap(capacity=cap, max_views=8, max_width=W, max_height=H)
+
+
+def test_stream_bookkeeping_and_convergence():
+    from paper_2504_02437_gb300 import stream as S
+    cams, tg, pts = stream_sequence(0, 8, W, H, FX)
+    gm = _map()
+    st = S.run_stream(gm, cams, tg, pts, window=4, iters=30, track_psnr="curve")
+    n, ins = st["n_gauss"], st["n_inserted"]
+    assert ins[0] == pts[0].shape[0] and n[0] >= ins[0]
+    for j in range(1, len(n)):
+        assert 0 <= ins[j] <= pts[j].shape[0]
+        assert n[j] - n[j - 1] - ins[j] >= 0          # each split replaces 1 parent by 2 children
+    assert sum(ins[1:]) > 0
+    # the newest keyframe's PSNR rises over its iterations
+    c = st["psnr"]
+    assert c.shape == (8, 30)
+    assert float((c[:, -1] - c[:, 0]).mean()) > 1.0
+    assert torch.isfinite(gm.params()).all()
+    assert len(st["iteration_ms"]) == 8 and all(len(x) == 30 for x in st["iteration_ms"])
+    gm.close()
+
+
+def test_densify_splits_in_stream():
+    """With a threshold below every visible Gaussian's statistic, every visible Gaussian splits."""
+    from paper_2504_02437_gb300 import stream as S
+    cams, tg, pts = stream_sequence(2, 3, W, H, FX)
+    from paper_2504_02437_gb300.api import GaussianMap
+    gm = GaussianMap(capacity=100_000, max_views=8, max_width=W, max_height=H, split_thresh=1e-9)
+    st = S.run_stream(gm, cams, tg, pts, window=2, iters=10)
+    assert st["n_gauss"][0] > st["n_inserted"][0]
+    gm.close()
+
+
+def test_learned_initialiser_reaches_plain_psnr_sooner():
+    """Full-size keyframes (640x480): an initialiser trained on one sequence's converged
+    Gaussians reaches, on a held-out sequence, the PSNR plain initialisation has after 100
+    iterations in fewer iterations on average."""
+    from paper_2504_02437_gb300 import stream as S
+    from paper_2504_02437_gb300.api import GaussianMap, MLP
+    iters = 100
+
+    def new():
+        return GaussianMap(capacity=1_000_000, max_views=8, max_width=640, max_height=480)
+    cams, tg, pts = stream_sequence(0, 30)
+    gm = new()
+    st = S.run_stream(gm, cams, tg, pts, iters=iters, collect=True)
+    gm.close()
+    X, Y = st["features"], st["targets"]
+    assert X.shape[0] == sum(st["n_inserted"]) and Y.shape == (X.shape[0], 16)
+    mlp = MLP(seed=0)
+    losses = S.train_mlp(mlp, X, Y, epochs=300, batch=1024)
+    assert losses[-1] < 0.5 * losses[0]
+    cams, tg, pts = stream_sequence(100, 12)
+    curves = {}
+    for name, m in (("plain", None), ("mlp", mlp)):
+        gm = new()
+        curves[name] = S.run_stream(gm, cams, tg, pts, iters=iters, track_psnr="curve", mlp=m)["psnr"][1:]
+        gm.close()
+    goal = curves["plain"][:, -1]
+    k = S.iterations_to_reach(curves["mlp"], goal).numpy()
+    assert np.mean(np.minimum(k, iters)) <= 0.92 * iters, k

@@ -14,7 +14,7 @@ import pytest
 import torch
 
 import oracle as O
-from synth import Camera, frustum_scene
+from synth import Camera, frustum_scene, random_target
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 CFG = O.Config()
@@ -502,10 +502,43 @@ def test_init_map_knn_excludes_self():
 
 
 def test_screen_grad_norms():
+    """Closed form at W = H = 2 (NDC = pixel units); the statistic scales with the image size."""
     g = [{"u": np.array([3.0, 0.0]), "v": np.array([4.0, 1.0])}, {"u": np.array([0.0, 6.0]), "v": np.array([0.0, 8.0])}]
-    s, c = O.screen_grad_norms(g, [np.array([True, True]), np.array([False, True])])
+    ok = [np.array([True, True]), np.array([False, True])]
+    s, c = O.screen_grad_norms(g, ok, [(2, 2), (2, 2)])
     np.testing.assert_allclose(s, [5.0, 11.0])
     np.testing.assert_allclose(c, [1, 2])
+    s2, _ = O.screen_grad_norms(g, ok, [(640, 480), (2, 2)])
+    np.testing.assert_allclose(s2, [math.hypot(3 * 320, 4 * 240), 240 + 10])
+
+
+def test_screen_grad_norm_is_ndc_gradient():
+    """The statistic equals the norm of a finite-difference gradient of the loss with respect to
+    the Gaussian's projected position in NDC. An isotropic Gaussian on the optical axis has a
+    footprint whose shape does not change to first order under a sideways shift of its mean,
+    so the shift only moves u (by fx dx / z pixels, i.e. 2 fx dx / (z W) in NDC)."""
+    p, cam = frustum_scene(n=1, width=32, height=24, fx=40.0, fy=44.0, cx=16.3, cy=12.4, seed=3)
+    z, h = 2.0, 1e-6
+    p[0:3, 0] = [0.0, 0.0, z]
+    p[3:6, 0] = -1.3
+    p[6:10, 0] = [1.0, 0.0, 0.0, 0.0]
+    p[10, 0] = 1.0
+    tg = random_target(32, 24, seed=4)
+    p64 = p.astype(np.float64)
+    ref = O.loss_and_grads(p64, [cam], tg, want_2d=True)
+    pr = O.project(torch.tensor(p64), cam)
+    s, c = O.screen_grad_norms(ref["grad2d"], [pr["valid"].numpy()], [(32, 24)])
+
+    def L(dx, dy):
+        q = p64.copy()
+        q[0, 0] += dx
+        q[1, 0] += dy
+        return O.loss_and_grads(q, [cam], tg)["loss"]
+    gx = (L(h, 0) - L(-h, 0)) / (2 * h) / (2 * cam.fx / (z * 32))
+    gy = (L(0, h) - L(0, -h)) / (2 * h) / (2 * cam.fy / (z * 24))
+    assert math.hypot(gx, gy) > 0
+    np.testing.assert_allclose(s[0], math.hypot(gx, gy), rtol=1e-5)
+    assert c[0] == 1
 
 
 # ------------------------------------------------------------------ learned initialiser
