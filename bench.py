@@ -436,6 +436,9 @@ TTP_METRIC = ("time-to-PSNR, learned vs plain initialisation: ms of mapping iter
               "reaches the PSNR plain initialisation has after 100 iterations (held-out sequences)")
 
 
+STREAM_CAPACITY = 1_500_000   # a 200-keyframe stream densifies to about 0.3M Gaussians
+
+
 def _stream_map(capacity, args):
     from paper_2504_02437_gb300.api import GaussianMap
     return GaussianMap(capacity=capacity, max_views=8, max_width=640, max_height=480, tile_size=args.tile,
@@ -456,7 +459,7 @@ def time_to_psnr(train_seeds, heldout_seeds, frames, iters, args, epochs=300, lo
     X, Y = [], []
     for sd in train_seeds:
         cams, tg, pts = stream_sequence(sd, frames)
-        gm = _stream_map(200_000, args)
+        gm = _stream_map(STREAM_CAPACITY, args)
         st = S.run_stream(gm, cams, tg, pts, iters=iters, collect=True)
         gm.close()
         X.append(st["features"])
@@ -476,7 +479,7 @@ def time_to_psnr(train_seeds, heldout_seeds, frames, iters, args, epochs=300, lo
         cams, tg, pts = stream_sequence(sd, frames)
         runs = {}
         for name, m in (("plain", None), ("mlp", mlp)):
-            gm = _stream_map(200_000, args)
+            gm = _stream_map(STREAM_CAPACITY, args)
             runs[name] = S.run_stream(gm, cams, tg, pts, iters=iters, track_psnr="curve", mlp=m)
             gm.close()
         cp, cm = runs["plain"]["psnr"][1:], runs["mlp"]["psnr"][1:]
@@ -522,11 +525,11 @@ def run_stream_bench(args):
     F, I = args.frames, 100
     # warm-up: a short stream of another sequence (builds, autotunes the small shapes)
     cams, tg, pts = stream_sequence(1, args.warmup)
-    gm = _stream_map(200_000, args)
+    gm = _stream_map(STREAM_CAPACITY, args)
     S.run_stream(gm, cams, tg, pts, iters=I)
     gm.close()
     cams, tg, pts = stream_sequence(0, F)
-    gm = _stream_map(200_000, args)
+    gm = _stream_map(STREAM_CAPACITY, args)
     with ClockSampler(0) as clk:
         st = S.run_stream(gm, cams, tg, pts, iters=I, track_psnr="final", flush=flush)
     tile, ppt = gm.tile_size, gm.pixels_per_thread

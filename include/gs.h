@@ -83,6 +83,10 @@ typedef struct gs_config {
     float split_thresh;  /* split if mean NDC position-grad norm > this (2e-4)        */
     float split_factor;  /* children log-scale -= ln(split_factor) (1.6)              */
     float insert_opacity;/* skip a new point if rendered opacity > this (0.99)        */
+    float insert_tau;    /* > 0: Eq. 7 distance rule instead of the opacity gate: insert
+                            iff the nearest existing mean is farther than this (0)    */
+    float clarity_sigma; /* > 0: Eq. 9 split mask, split a Gaussian that dominates more
+                            than this many pixels (gs_count_dominant) (0 = off)       */
     int32_t tile_size;   /* 8 or 16 pixels; 0 = pick by the built-in autotuner        */
     int32_t pixels_per_thread; /* compositing kernels: 1, 2 or 4 (16-px tiles), 1 or 2
                                   (8-px tiles); 0 = the autotuner's or the default      */
@@ -181,9 +185,11 @@ GS_API int gs_iterate(gs_ctx* ctx, const gs_camera* cams_host, int n_views, cons
  * is skipped; every other point is appended with the plain initialisation
  * (log-scale from the 3 nearest existing means, colour of image_dev
  * [3][H][W] at the point's pixel), or the learned initialiser when one is
- * set (gs_set_initializer). Writes the number appended to *n_inserted_host
- * and, when inserted_dev is not NULL, 1 or 0 per point to inserted_dev [n].
- * Synchronises the stream. */
+ * set (gs_set_initializer). With insert_tau > 0 the distance rule of Eq. 7's
+ * text replaces the opacity gate (nothing is rendered): a point is appended
+ * iff its nearest existing Gaussian mean is farther than insert_tau. Writes
+ * the number appended to *n_inserted_host and, when inserted_dev is not
+ * NULL, 1 or 0 per point to inserted_dev [n]. Synchronises the stream. */
 GS_API int gs_insert(gs_ctx* ctx, const gs_camera* cam_host, const float* image_dev, const float* points_dev,
                      int n, int* n_inserted_host, uint8_t* inserted_dev, void* stream);
 
@@ -237,6 +243,14 @@ GS_API int gs_set_initializer(gs_ctx* ctx, gs_mlp* mlp);
  * with the context's counter-based generator). Resets the statistics.
  * Writes the number of split parents to *n_split_host. Synchronises. */
 GS_API int gs_densify(gs_ctx* ctx, const float* normals_dev, int* n_split_host, void* stream);
+
+/* Eq. 8-9 (Section 3.2 "Clarity-Enhancing Gaussian Densification"): renders
+ * the views (cams_host: n_views cameras of one image size) with the per-pixel
+ * argmax of the blend weight w_m (Eq. 8) and adds, per Gaussian, the number of
+ * pixels it dominates to its count. gs_densify then also splits every
+ * Gaussian whose count exceeds clarity_sigma (when > 0) and resets the counts.
+ * Synchronises. Errors: GS_ERR_ARG, GS_ERR_OOM, GS_ERR_CUDA. */
+GS_API int gs_count_dominant(gs_ctx* ctx, const gs_camera* cams_host, int n_views, void* stream);
 
 /* Device-side timing of the path's phases with CUDA events recorded on the
  * launching stream around each phase's kernels (a profiling aid; off by

@@ -21,7 +21,10 @@ Passages followed
 * Eq. 8 (Section 3.2, Clarity-Enhancing Densification): the blend weight
   w_m = alpha_m prod_{n<m}(1 - alpha_n) and the per-pixel argmax id.
 * Eq. 10-11 (Section 3.2, Map Optimization): L_photo = L1, the planar term
-  L_reg = |max(0.01, min(s))| and L = lambda_color L_color + lambda_reg L_reg.
+  L_reg = |max(0.01, min(s))| and L = lambda_color L_color + lambda_reg L_reg;
+  L_color = (1 - lambda_photo) L1 + lambda_photo L_SSIM with L_SSIM = 1 - SSIM
+  (the lineage's 11 x 11 Gaussian window, sigma 1.5, C1 = 0.01^2, C2 = 0.03^2,
+  zero padding). lambda_photo = 0 (pure L1) unless set; the paper's is 0.2.
 * Eq. 6-7 (Section 3.2, Map Initialization / Dynamic Insertion): the new points
   are back-projected patch centres; which of them become Gaussians follows the
   opacity reading below.
@@ -80,6 +83,7 @@ class Config:
     T_min: float = 1e-4
     lambda_color: float = 1.0
     lambda_reg: float = 1.0
+    lambda_photo: float = 0.0       # Eq. 10 weight of L_SSIM = 1 - SSIM (0.2 in the paper; 0 = pure L1)
     reg_floor: float = 0.01
     beta1: float = 0.9
     beta2: float = 0.999
@@ -87,7 +91,9 @@ class Config:
     lr: tuple = (1e-3, 5e-3, 1e-3, 5e-2, 2.5e-3)   # means, log-scales, quats, opacity, colours
     split_thresh: float = 2e-4
     split_factor: float = 1.6
+    clarity_sigma: float = 0.0      # Eq. 9 threshold sigma in pixels (0 = clarity split off)
     insert_opacity: float = 0.99
+    insert_tau: float = 0.0         # Eq. 7 distance threshold tau in metres (0 = opacity rule)
 
 
 def _t(x) -> torch.Tensor:
@@ -391,6 +397,43 @@ def render(params, cam, cfg: Config = Config(), chunk: int = 1024, pixels=None, 
 # ------------------------------------------------------------------ Eq. 10-11: loss
 
 
+SSIM_SIZE, SSIM_SIGMA, SSIM_C1, SSIM_C2 = 11, 1.5, 0.01 ** 2, 0.03 ** 2
+
+
+def ssim_window() -> torch.Tensor:
+    """The 11 x 11 Gaussian window (sigma 1.5) of the SSIM of the 3DGS lineage, normalised to
+    sum 1: the outer product of the normalised 1D Gaussian with itself."""
+    k = torch.arange(SSIM_SIZE, dtype=DT) - SSIM_SIZE // 2
+    g = torch.exp(-k * k / (2.0 * SSIM_SIGMA ** 2))
+    g = g / g.sum()
+    return torch.outer(g, g)
+
+
+def ssim_map(x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
+    """Per-pixel, per-channel SSIM of images x, y [3, H, W] (Wang et al. 2004): local means,
+    variances and covariance under the window, zero padding outside the image.
+    SSIM = (2 mu_x mu_y + C1)(2 s_xy + C2) / ((mu_x^2 + mu_y^2 + C1)(s_xx + s_yy + C2))."""
+    w = ssim_window()[None, None].expand(3, 1, SSIM_SIZE, SSIM_SIZE)
+    pad = SSIM_SIZE // 2
+
+    def blur(z):
+        return torch.nn.functional.conv2d(z[None], w, padding=pad, groups=3)[0]
+    mx, my = blur(x), blur(y)
+    sxx = blur(x * x) - mx * mx
+    syy = blur(y * y) - my * my
+    sxy = blur(x * y) - mx * my
+    return ((2 * mx * my + SSIM_C1) * (2 * sxy + SSIM_C2)) / ((mx * mx + my * my + SSIM_C1) * (sxx + syy + SSIM_C2))
+
+
+def color_loss(img: torch.Tensor, target: torch.Tensor, cfg: Config = Config()) -> torch.Tensor:
+    """Eq. 10 L_color of one view: (1 - lambda_photo) mean|C - I| + lambda_photo (1 - mean SSIM),
+    means over the 3HW channel-pixels."""
+    l1 = (img - target).abs().mean()
+    if cfg.lambda_photo == 0:
+        return l1
+    return (1.0 - cfg.lambda_photo) * l1 + cfg.lambda_photo * (1.0 - ssim_map(img, target).mean())
+
+
 def planar_reg(params, cfg: Config = Config()) -> torch.Tensor:
     """Eq. 10 planar term, averaged over the N Gaussians: mean_i max(0.01, min_k s_ik)."""
     s = torch.exp(params[ROW_LOGSCALE])
@@ -429,13 +472,31 @@ def loss_and_grads(params, cams: Sequence, targets, cfg: Config = Config(), chun
         Tv = np.zeros(pix.shape[0])
         lastv = np.zeros(pix.shape[0], np.int64)
         scale = cfg.lambda_color / (3.0 * H * W)
+        up = None
+        if cfg.lambda_photo != 0:
+            # L_SSIM couples neighbouring pixels: take dL/dC of the whole image first, then
+            # propagate it through the compositing chunk by chunk (chain rule)
+            assert pixels is None, "the SSIM term needs the whole image"
+            with torch.no_grad():
+                full = torch.zeros(pix.shape[0], 3, dtype=DT)
+                for s in range(0, pix.shape[0], chunk):
+                    cp = pix[s:s + chunk]
+                    full[s:s + chunk] = composite(cp[:, 0], cp[:, 1], prl, cfg, order)["rgb"]
+            C_img = full.T.reshape(3, H, W).clone().requires_grad_(True)
+            lc = cfg.lambda_color * color_loss(C_img, torch.as_tensor(tg[vi], dtype=DT), cfg)
+            lc.backward()
+            total = total + lc.detach()
+            up = C_img.grad.reshape(3, -1).T
         for s in range(0, pix.shape[0], chunk):
             cp = pix[s:s + chunk]
             res = composite(cp[:, 0], cp[:, 1], prl, cfg, order, flags=flags)
-            I = torch.as_tensor(tg[vi][:, cp[:, 1], cp[:, 0]].T, dtype=DT)
-            l1 = scale * (res["rgb"] - I).abs().sum()
-            l1.backward()
-            total = total + l1.detach()
+            if up is None:
+                I = torch.as_tensor(tg[vi][:, cp[:, 1], cp[:, 0]].T, dtype=DT)
+                l1 = scale * (res["rgb"] - I).abs().sum()
+                l1.backward()
+                total = total + l1.detach()
+            else:
+                (res["rgb"] * up[s:s + chunk]).sum().backward()
             img[s:s + chunk] = res["rgb"].detach().numpy()
             Tv[s:s + chunk] = res["T"].detach().numpy()
             lastv[s:s + chunk] = res["last"].numpy()
@@ -474,7 +535,7 @@ def loss_value(params, cams, targets, cfg: Config = Config(), chunk: int = 1024)
     with torch.no_grad():
         for vi, cam in enumerate(cams):
             img = render(p, cam, cfg, chunk=chunk)["rgb"]
-            total += cfg.lambda_color * np.abs(img - tg[vi]).sum() / (3.0 * cam.height * cam.width)
+            total += cfg.lambda_color * float(color_loss(_t(img), _t(tg[vi]), cfg))
         total += cfg.lambda_reg * float(planar_reg(p, cfg))
     return float(total)
 
@@ -556,6 +617,22 @@ def insertion_mask(points, cam, T_final, cfg: Config = Config()):
     return ~skip, np.stack([pi, pj], 1), inside
 
 
+def distance_insertion_mask(points, means, cfg: Config = Config()):
+    """Eq. 7 as the text states it (the equation's d < tau reads the other way): a new point q
+    becomes a Gaussian iff d(q, P) = min over the existing Gaussian means p of |q - p|_2 exceeds
+    ``insert_tau``; into an empty map every point is inserted. Returns (mask bool [n], d [n]);
+    d is +inf for an empty map."""
+    X = np.asarray(points, np.float64).reshape(-1, 3)
+    E = np.asarray(means, np.float64).reshape(-1, 3)
+    if E.shape[0] == 0:
+        return np.ones(X.shape[0], bool), np.full(X.shape[0], np.inf)
+    d = np.full(X.shape[0], np.inf)
+    for s0 in range(0, E.shape[0], 4096):
+        blk = E[s0:s0 + 4096]
+        d = np.minimum(d, np.sqrt(((X[:, None, :] - blk[None, :, :]) ** 2).sum(-1)).min(1))
+    return d > cfg.insert_tau, d
+
+
 def plain_init(points, pixels, image, existing_means):
     """Initial parameters [14, n] of inserted Gaussians (the plain initialisation reading).
 
@@ -621,8 +698,23 @@ def screen_grad_norms(grad2d_views, valid_views, sizes):
 # ------------------------------------------------------------------ densification split (gradient reading)
 
 
-def split(params, m, v, grad_sum, grad_cnt, normals, cfg: Config = Config()):
-    """Split every Gaussian whose mean NDC position-gradient norm exceeds ``split_thresh``.
+def dominance_counts(argmax_maps, n):
+    """Eq. 8-9 (clarity-enhancing densification), read as: O_i(n) is the set of pixels of view i
+    that Gaussian n renders, O_i(m) the set of pixels whose largest blend weight w_m (Eq. 8)
+    belongs to n, so |O_i(n) & O_i(m)| is the number of pixels Gaussian n dominates. Returns
+    that number per Gaussian, summed over the given per-view argmax maps (-1 = no Gaussian)."""
+    c = np.zeros(n, np.int64)
+    for a in argmax_maps:
+        a = np.asarray(a).ravel()
+        a = a[a >= 0]
+        c += np.bincount(a, minlength=n)[:n]
+    return c
+
+
+def split(params, m, v, grad_sum, grad_cnt, normals, cfg: Config = Config(), dominant=None):
+    """Split every Gaussian whose mean NDC position-gradient norm exceeds ``split_thresh``, and,
+    when ``dominant`` (per-Gaussian dominated-pixel counts) is given and ``clarity_sigma`` > 0,
+    every Gaussian that dominates more than ``clarity_sigma`` pixels (the split mask M of Eq. 9).
 
     mean = grad_sum / grad_cnt over the iterations in which it was visible (0 if never).
     Each split parent is replaced by two children with means mu + R S z_k (z_k the given
@@ -635,6 +727,8 @@ def split(params, m, v, grad_sum, grad_cnt, normals, cfg: Config = Config()):
     cnt = np.asarray(grad_cnt, np.float64)
     mean_g = np.where(cnt > 0, np.asarray(grad_sum, np.float64) / np.maximum(cnt, 1), 0.0)
     mask = mean_g > cfg.split_thresh
+    if dominant is not None and cfg.clarity_sigma > 0:
+        mask = mask | (np.asarray(dominant) > cfg.clarity_sigma)
     ids = np.nonzero(mask)[0]
     with torch.no_grad():
         R = quat_to_rotmat(_t(P[ROW_QUAT, ids].T)).numpy()

@@ -36,7 +36,8 @@ class gs_config(C.Structure):
                 ("alpha_max", C.c_float), ("T_min", C.c_float), ("lambda_color", C.c_float),
                 ("lambda_reg", C.c_float), ("reg_floor", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
                 ("eps", C.c_float), ("lr", C.c_float * 5), ("split_thresh", C.c_float),
-                ("split_factor", C.c_float), ("insert_opacity", C.c_float), ("tile_size", C.c_int32), ("pixels_per_thread", C.c_int32),
+                ("split_factor", C.c_float), ("insert_opacity", C.c_float), ("insert_tau", C.c_float),
+                ("clarity_sigma", C.c_float), ("tile_size", C.c_int32), ("pixels_per_thread", C.c_int32),
                 ("capacity", C.c_int32), ("max_views", C.c_int32), ("max_width", C.c_int32),
                 ("max_height", C.c_int32), ("pair_capacity", C.c_int64), ("seed", C.c_uint64)]
 
@@ -58,6 +59,7 @@ SIGNATURES = {
     "gs_backward": (_I, [_P, _P, _P]),
     "gs_step": (_I, [_P, _P]),
     "gs_iterate": (_I, [_P, C.POINTER(gs_camera), _I, _P, _P, _P, _P]),
+    "gs_count_dominant": (_I, [_P, C.POINTER(gs_camera), _I, _P]),
     "gs_insert": (_I, [_P, C.POINTER(gs_camera), _P, _P, _I, C.POINTER(_I), _P, _P]),
     "gs_densify": (_I, [_P, _P, C.POINTER(_I), _P]),
     "gs_debug_projection": (_I, [_P, _I, _P]),

@@ -171,8 +171,9 @@ class GaussianMap:
 
     # ---- map management
     def insert(self, cam, image: torch.Tensor, points: torch.Tensor, return_mask: bool = False):
-        """Insert the points that are not behind rendered opacity > 0.99; returns the count
-        (and the per-point inserted mask with ``return_mask``)."""
+        """Insert the points that are not behind rendered opacity > insert_opacity (or, with
+        insert_tau > 0, that lie farther than insert_tau from every existing mean); returns
+        the count (and the per-point inserted mask with ``return_mask``)."""
         arr, V, H, W = _cams([cam])
         pts = points.to(torch.float32).contiguous()
         img = image.to(torch.float32).contiguous()
@@ -186,6 +187,11 @@ class GaussianMap:
         """Use the learned initialiser for insertions (None: the plain initialisation)."""
         self._init_mlp = mlp
         self._check(self.lib.gs_set_initializer(self.ctx, mlp.handle if mlp is not None else None))
+
+    def count_dominant(self, cams):
+        """Add each Gaussian's dominated pixels in these views (Eq. 8-9) to its count."""
+        arr, V, H, W = _cams(cams)
+        self._check(self.lib.gs_count_dominant(self.ctx, arr, V, _stream()))
 
     def densify(self, normals: Optional[torch.Tensor] = None) -> int:
         nz = None if normals is None else normals.to(torch.float32).contiguous()

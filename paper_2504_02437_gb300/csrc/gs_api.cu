@@ -347,6 +347,7 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         ok = ok && dalloc(&c->adam_v, kParamRows * cap) == cudaSuccess;
         ok = ok && dalloc(&c->dens_sum, cap) == cudaSuccess;
         ok = ok && dalloc(&c->dens_cnt, cap) == cudaSuccess;
+        ok = ok && dalloc(&c->dom_cnt, cap) == cudaSuccess;
         ok = ok && dalloc(&c->dcam, V) == cudaSuccess;
         ok = ok && dalloc(&c->rec, 3 * V * cap) == cudaSuccess;
         ok = ok && dalloc(&c->tiles_touched, V * cap) == cudaSuccess;
@@ -380,6 +381,7 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         if (e == cudaSuccess) e = cudaMemset(c->grad2d, 0, sizeof(float) * kGrad2dStride * V * cap);
         if (e == cudaSuccess) e = cudaMemset(c->dens_sum, 0, sizeof(float) * cap);
         if (e == cudaSuccess) e = cudaMemset(c->dens_cnt, 0, sizeof(float) * cap);
+        if (e == cudaSuccess) e = cudaMemset(c->dom_cnt, 0, sizeof(uint32_t) * cap);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) { code = fail(c, GS_ERR_CUDA, "initialisation", e); break; }
     } while (0);
@@ -400,7 +402,7 @@ void gs_destroy(gs_ctx* c) {
         cudaEventDestroy(r.b);
     }
     for (auto e : c->tpool) cudaEventDestroy(e);
-    void* ptrs[] = {c->params, c->grads, c->adam_m, c->adam_v, c->dens_sum, c->dens_cnt, c->dcam, c->rec,
+    void* ptrs[] = {c->params, c->grads, c->adam_m, c->adam_v, c->dens_sum, c->dens_cnt, c->dom_cnt, c->dcam, c->rec,
                     c->tiles_touched, c->depth, c->dkey[0], c->dkey[1], c->dval[0], c->dval[1], c->offsets, c->ranges,
                     c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->dcount, c->partials, c->fpart,
                     c->own_rgb};
@@ -436,6 +438,7 @@ int gs_set_params(gs_ctx* c, const float* params_dev, int n, void* stream) {
     CK(cudaMemsetAsync(c->adam_v, 0, sizeof(float) * kParamRows * c->cap, s));
     CK(cudaMemsetAsync(c->dens_sum, 0, sizeof(float) * c->cap, s));
     CK(cudaMemsetAsync(c->dens_cnt, 0, sizeof(float) * c->cap, s));
+    CK(cudaMemsetAsync(c->dom_cnt, 0, sizeof(uint32_t) * c->cap, s));
     CK(cudaMemsetAsync(c->dcount + 4, 0, sizeof(uint32_t), s));
     c->n = n;
     c->adam_t = 0;
@@ -544,9 +547,12 @@ int gs_step(gs_ctx* c, void* stream) {
     return GS_OK;
 }
 
-// The autotuner: times render + loss + adjoint (no Adam step, so the map is
-// unchanged) for each (tile size, pixels per thread) candidate on the caller's
-// views and keeps the fastest for this (image size, views, N-bucket).
+// The autotuner: for each (tile size, pixels per thread) candidate on the
+// caller's views, one plain render sizes the pair buffers, then the part of the
+// mapping iteration that depends on the layout (projection, binning, sort and
+// the fused compositing + L1 + adjoint kernel) is timed; the fastest is kept
+// for this (image size, views, N-bucket). The adjoint of the projection and
+// Adam are left out, so the map and its statistics are unchanged.
 static int autotune(gs_ctx* c, const gs_camera* cams, int n_views, const float* target, float* rgb,
                     cudaStream_t s) {
     static const int cand[][2] = {{16, 1}, {16, 2}, {16, 4}, {8, 1}, {8, 2}};
@@ -561,11 +567,20 @@ static int autotune(gs_ctx* c, const gs_camera* cams, int n_views, const float* 
         c->force_tile = cd[0];
         c->force_ppt = cd[1];
         float ms = 0.f;
+        code = gs_render(c, cams, n_views, rgb, nullptr, nullptr, s);
+        const DevConst k = dev_const(c->cfg);
         for (int rep = 0; rep < 2 && code == GS_OK; ++rep) {
             cudaEventRecord(e0, s);
-            code = gs_render(c, cams, n_views, rgb, nullptr, nullptr, s);
-            if (code == GS_OK) code = gs_loss(c, target, nullptr, s);
-            if (code == GS_OK) code = gs_backward(c, nullptr, s);
+            code = setup_views(c, cams, n_views, s);
+            if (code == GS_OK) code = front_half(c, k, s);
+            if (code == GS_OK) code = back_half(c, k, nullptr, nullptr, s);
+            if (code == GS_OK &&
+                cudaMemsetAsync(c->grad2d, 0, sizeof(float) * kGrad2dStride * c->n_views * (size_t)c->n, s) !=
+                    cudaSuccess)
+                code = GS_ERR_CUDA;
+            int fgrid = 0;
+            if (code == GS_OK && launch_raster_fused(c, k, target, rgb, c->fpart, c->n_fpart, &fgrid, s) != cudaSuccess)
+                code = GS_ERR_CUDA;
             cudaEventRecord(e1, s);
             if (cudaEventSynchronize(e1) != cudaSuccess) code = GS_ERR_CUDA;
             if (rep == 1) cudaEventElapsedTime(&ms, e0, e1);
@@ -964,6 +979,7 @@ int gs_init_map(gs_ctx* c, const float* pts, const float* rgb, int n, void* stre
         CK(cudaMemset2DAsync(a + c->n, sizeof(float) * c->cap, 0, sizeof(float) * n, kParamRows, s));
     CK(cudaMemsetAsync(c->dens_sum + c->n, 0, sizeof(float) * n, s));
     CK(cudaMemsetAsync(c->dens_cnt + c->n, 0, sizeof(float) * n, s));
+    CK(cudaMemsetAsync(c->dom_cnt + c->n, 0, sizeof(uint32_t) * n, s));
     CK(cudaStreamSynchronize(s));
     c->n += n;
     invalidate_render(c);
@@ -997,8 +1013,15 @@ int gs_insert(gs_ctx* c, const gs_camera* cam, const float* image, const float* 
     if (!t.get(&img, 3 * HW) || !t.get(&stage, kParamRows * (size_t)n) || !t.get(&keep, (size_t)n) ||
         !t.get(&pos, (size_t)n) || !t.get(&feat, 80 * (size_t)n))
         return fail(c, GS_ERR_OOM, "temporary buffers");
-    int code = gs_render(c, cam, 1, img, nullptr, nullptr, stream);
-    if (code != GS_OK) return code;
+    if (c->cfg.insert_tau > 0.f) {
+        // distance rule: no render, only the camera (pixel colours of the plain initialisation)
+        CamBatch b;
+        const int code = prepare_views(c, cam, 1, b);
+        if (code != GS_OK) return code;
+    } else {
+        const int code = gs_render(c, cam, 1, img, nullptr, nullptr, stream);
+        if (code != GS_OK) return code;
+    }
     CK(launch_insert_test(c, c->hcam[0], pts, n, image, keep, stage, s));
     if (c->init_mlp) CK(mlp_initialise(c->init_mlp, c->hcam[0], image, pts, n, stage, feat, s));
     if (inserted_dev) {
@@ -1012,6 +1035,24 @@ int gs_insert(gs_ctx* c, const gs_camera* cam, const float* image, const float* 
     *n_ins = (int)c->hcount[5];
     c->n += *n_ins;
     invalidate_render(c);
+    return GS_OK;
+}
+
+int gs_count_dominant(gs_ctx* c, const gs_camera* cams, int n_views, void* stream) {
+    if (!c) return GS_ERR_ARG;
+    if (!cams || n_views < 1 || n_views > c->cfg.max_views) return fail(c, GS_ERR_ARG, "bad views");
+    if (c->n == 0) return GS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(c->device));
+    const size_t pix = (size_t)n_views * cams[0].width * cams[0].height;
+    Temp t;
+    float* img = nullptr;
+    int32_t* am = nullptr;
+    if (!t.get(&img, 3 * pix) || !t.get(&am, pix)) return fail(c, GS_ERR_OOM, "temporary buffers");
+    const int code = gs_render(c, cams, n_views, img, nullptr, am, stream);
+    if (code != GS_OK) return code;
+    CK(launch_count_dominant(c, am, pix, s));
+    CK(cudaStreamSynchronize(s));
     return GS_OK;
 }
 
@@ -1061,6 +1102,7 @@ int gs_densify(gs_ctx* c, const float* normals, int* n_split_out, void* stream) 
     }
     CK(cudaMemsetAsync(c->dens_sum, 0, sizeof(float) * c->cap, s));
     CK(cudaMemsetAsync(c->dens_cnt, 0, sizeof(float) * c->cap, s));
+    CK(cudaMemsetAsync(c->dom_cnt, 0, sizeof(uint32_t) * c->cap, s));
     CK(cudaStreamSynchronize(s));
     *n_split_out = (int)n_split;
     invalidate_render(c);

@@ -72,6 +72,7 @@ struct gs_ctx {
     float* adam_v = nullptr;
     float* dens_sum = nullptr;  // [cap] sum of screen-space gradient norms
     float* dens_cnt = nullptr;  // [cap] number of visible backward passes
+    uint32_t* dom_cnt = nullptr;  // [cap] dominated pixels counted by gs_count_dominant (Eq. 9)
 
     // per-render state
     int n_views = 0;            // views of the last render (0 = none)
@@ -198,6 +199,7 @@ cudaError_t launch_insert_test(gs_ctx* c, const DevCamera& cam, const float* pts
                                uint32_t* keep, float* stage, cudaStream_t s);
 cudaError_t launch_append(gs_ctx* c, const float* stage, int n_stage, const uint32_t* keep, const uint32_t* pos,
                           cudaStream_t s);
+cudaError_t launch_count_dominant(gs_ctx* c, const int32_t* argmax, size_t n_pix, cudaStream_t s);
 cudaError_t launch_split_flags(gs_ctx* c, uint32_t* flags, cudaStream_t s);
 cudaError_t launch_split_scatter(gs_ctx* c, const uint32_t* flags, const uint32_t* pos, uint32_t n_split,
                                  const float* normals, float* P2, float* M2, float* V2, cudaStream_t s);

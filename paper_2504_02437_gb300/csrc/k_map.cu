@@ -1,15 +1,19 @@
 // Map management: initialisation from back-projected points (Eq. 6), dynamic
 // insertion gated by rendered opacity (Eq. 7 reading) and densification by
 // splitting (Section 3.2). These run once per keyframe, not per iteration.
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gs {
 namespace {
 
 // 3 smallest squared distances from q to the reference points (one CTA per query).
-// ref is planar [3][ref_stride]; skip index `self` (or -1).
+// ref is planar [3][ref_stride]; skip index `self` (or -1). Returns the RMS of
+// those distances (0.01 if there is no reference point) to every thread, and
+// the smallest squared distance (+inf if none) in *dmin2 of thread 0.
 __device__ float knn3_rms(const float* __restrict__ ref, int ref_stride, int n_ref, float qx, float qy, float qz,
-                          int self) {
+                          int self, float* dmin2) {
     __shared__ float best[256 * 3];
     float b0 = INFINITY, b1 = INFINITY, b2 = INFINITY;
     for (int j = threadIdx.x; j < n_ref; j += blockDim.x) {
@@ -53,6 +57,7 @@ __device__ float knn3_rms(const float* __restrict__ ref, int ref_stride, int n_r
                 }
             }
         }
+        *dmin2 = c0;
         int cnt = (c0 < INFINITY) + (c1 < INFINITY) + (c2 < INFINITY);
         float s = (cnt > 0 ? c0 : 0.f) + (cnt > 1 ? c1 : 0.f) + (cnt > 2 ? c2 : 0.f);
         rms = cnt > 0 ? sqrtf(s / (float)cnt) : 0.01f;
@@ -67,7 +72,8 @@ __global__ void __launch_bounds__(256) k_init_points(const float* __restrict__ p
                                                      int ref_is_self, float* __restrict__ out, int out_stride) {
     int i = blockIdx.x;
     float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
-    float rms = knn3_rms(ref, ref_stride, n_ref, x, y, z, ref_is_self ? i : -1);
+    float dmin2;
+    float rms = knn3_rms(ref, ref_stride, n_ref, x, y, z, ref_is_self ? i : -1, &dmin2);
     if (threadIdx.x == 0) {
         float ls = fminf(fmaxf(logf(fmaxf(rms, 1e-30f)), -7.f), -1.f);
         const float v[kParamRows] = {x, y, z, ls, ls, ls, 1.f, 0.f, 0.f, 0.f, 0.f, rgb[3 * i], rgb[3 * i + 1],
@@ -76,17 +82,20 @@ __global__ void __launch_bounds__(256) k_init_points(const float* __restrict__ p
     }
 }
 
-// Opacity gate of the insertion: keep[i] = 0 iff point i projects, in front of
-// the camera, to a pixel whose rendered opacity 1 - T exceeds the threshold.
-// Also stages the plain initial parameters [14][n] of every point.
-__global__ void __launch_bounds__(256) k_insert_test(DevCamera cam, float near_z, float thresh,
+// Insertion test of point i. Opacity gate (tau2 = 0): keep[i] = 0 iff the point
+// projects, in front of the camera, to a pixel whose rendered opacity 1 - T
+// exceeds the threshold. Distance rule (tau2 = tau^2 > 0, Eq. 7 as its text
+// states it): keep[i] = 1 iff the nearest existing mean is farther than tau
+// (T is not read). Also stages the plain initial parameters [14][n].
+__global__ void __launch_bounds__(256) k_insert_test(DevCamera cam, float near_z, float thresh, float tau2,
                                                      const float* __restrict__ pts, const float* __restrict__ T,
                                                      const float* __restrict__ image, const float* __restrict__ ref,
                                                      int ref_stride, int n_ref, uint32_t* __restrict__ keep,
                                                      float* __restrict__ stage, int n) {
     int i = blockIdx.x;
     float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
-    float rms = knn3_rms(ref, ref_stride, n_ref, x, y, z, -1);
+    float dmin2 = INFINITY;
+    float rms = knn3_rms(ref, ref_stride, n_ref, x, y, z, -1, &dmin2);
     if (threadIdx.x != 0) return;
     float tx = cam.R[0] * x + cam.R[1] * y + cam.R[2] * z + cam.t[0];
     float ty = cam.R[3] * x + cam.R[4] * y + cam.R[5] * z + cam.t[1];
@@ -98,7 +107,7 @@ __global__ void __launch_bounds__(256) k_insert_test(DevCamera cam, float near_z
     bool inside = front && pxf >= 0.f && pxf < (float)cam.width && pyf >= 0.f && pyf < (float)cam.height;
     int px = inside ? (int)pxf : 0, py = inside ? (int)pyf : 0;
     size_t HW = (size_t)cam.width * cam.height, pix = (size_t)py * cam.width + px;
-    bool skip = inside && (1.f - T[pix]) > thresh;
+    bool skip = tau2 > 0.f ? !(dmin2 > tau2) : (inside && (1.f - T[pix]) > thresh);
     keep[i] = skip ? 0u : 1u;
     float ls = fminf(fmaxf(logf(fmaxf(rms, 1e-30f)), -7.f), -1.f);
     const float vals[kParamRows] = {x, y, z, ls, ls, ls, 1.f, 0.f, 0.f, 0.f, 0.f,
@@ -109,8 +118,8 @@ __global__ void __launch_bounds__(256) k_insert_test(DevCamera cam, float near_z
 __global__ void __launch_bounds__(256) k_append(const float* __restrict__ stage, int n_stage,
                                                 const uint32_t* __restrict__ keep, const uint32_t* __restrict__ pos,
                                                 float* __restrict__ P, float* __restrict__ M, float* __restrict__ V,
-                                                float* __restrict__ dsum, float* __restrict__ dcnt, int base,
-                                                int cap) {
+                                                float* __restrict__ dsum, float* __restrict__ dcnt,
+                                                uint32_t* __restrict__ dom, int base, int cap) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_stage || !keep[i]) return;
     int d = base + (int)pos[i];
@@ -121,15 +130,30 @@ __global__ void __launch_bounds__(256) k_append(const float* __restrict__ stage,
     }
     dsum[d] = 0.f;
     dcnt[d] = 0.f;
+    dom[d] = 0u;
 }
 
+// Split mask: the gradient criterion, or (sigma > 0) more than sigma dominated
+// pixels (Eq. 9 split mask M).
 __global__ void __launch_bounds__(256) k_split_flags(const float* __restrict__ dsum, const float* __restrict__ dcnt,
-                                                     int n, float thresh, uint32_t* __restrict__ flags) {
+                                                     const uint32_t* __restrict__ dom, int n, float thresh,
+                                                     float sigma, uint32_t* __restrict__ flags) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float c = dcnt[i];
     float mean = c > 0.f ? dsum[i] / c : 0.f;
-    flags[i] = mean > thresh ? 1u : 0u;
+    const bool clear = sigma > 0.f && (float)dom[i] > sigma;
+    flags[i] = (mean > thresh || clear) ? 1u : 0u;
+}
+
+// Eq. 8-9: every pixel whose largest blend weight belongs to Gaussian a adds one
+// to a's dominated-pixel count (argmax -1: no Gaussian).
+__global__ void __launch_bounds__(256) k_count_dominant(const int32_t* __restrict__ argmax, size_t n_pix, int n,
+                                                        uint32_t* __restrict__ dom) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n_pix; i += (size_t)gridDim.x * blockDim.x) {
+        const int a = argmax[i];
+        if (a >= 0 && a < n) atomicAdd(dom + a, 1u);
+    }
 }
 
 // SplitMix64 (Steele, Lea and Flood 2014) as a counter-based generator.
@@ -224,8 +248,9 @@ cudaError_t launch_insert_test(gs_ctx* c, const DevCamera& cam, const float* pts
                                uint32_t* keep, float* stage, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     ++c->launches;
-    k_insert_test<<<n, 256, 0, s>>>(cam, c->cfg.near_z, c->cfg.insert_opacity, pts, c->T_final, image, c->params,
-                                    c->cap, c->n, keep, stage, n);
+    const float tau2 = c->cfg.insert_tau > 0.f ? c->cfg.insert_tau * c->cfg.insert_tau : 0.f;
+    k_insert_test<<<n, 256, 0, s>>>(cam, c->cfg.near_z, c->cfg.insert_opacity, tau2, pts, c->T_final, image,
+                                    c->params, c->cap, c->n, keep, stage, n);
     return cudaGetLastError();
 }
 
@@ -234,14 +259,23 @@ cudaError_t launch_append(gs_ctx* c, const float* stage, int n_stage, const uint
     if (n_stage == 0) return cudaSuccess;
     ++c->launches;
     k_append<<<(n_stage + 255) / 256, 256, 0, s>>>(stage, n_stage, keep, pos, c->params, c->adam_m, c->adam_v,
-                                                   c->dens_sum, c->dens_cnt, c->n, c->cap);
+                                                   c->dens_sum, c->dens_cnt, c->dom_cnt, c->n, c->cap);
     return cudaGetLastError();
 }
 
 cudaError_t launch_split_flags(gs_ctx* c, uint32_t* flags, cudaStream_t s) {
     if (c->n == 0) return cudaSuccess;
     ++c->launches;
-    k_split_flags<<<(c->n + 255) / 256, 256, 0, s>>>(c->dens_sum, c->dens_cnt, c->n, c->cfg.split_thresh, flags);
+    k_split_flags<<<(c->n + 255) / 256, 256, 0, s>>>(c->dens_sum, c->dens_cnt, c->dom_cnt, c->n,
+                                                     c->cfg.split_thresh, c->cfg.clarity_sigma, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_dominant(gs_ctx* c, const int32_t* argmax, size_t n_pix, cudaStream_t s) {
+    if (n_pix == 0 || c->n == 0) return cudaSuccess;
+    ++c->launches;
+    const int grid = (int)std::min<size_t>((n_pix + 255) / 256, (size_t)c->num_sms * 8);
+    k_count_dominant<<<grid, 256, 0, s>>>(argmax, n_pix, c->n, c->dom_cnt);
     return cudaGetLastError();
 }
 

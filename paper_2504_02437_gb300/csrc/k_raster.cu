@@ -125,11 +125,39 @@ __device__ __forceinline__ float warp_sum9(const float (&v)[9], int lane, int& i
 
 // Shared-memory staging of one batch of raster records, shared by the forward
 // and backward passes of a CTA.
+constexpr int kMaxWarps = 8;  // 256 threads per CTA at most
+
 struct Stage {
     float4 s0[kBatch], s1[kBatch], s2[kBatch];
     uint32_t sid[kBatch];
     uint32_t mask[kBatch];   // bit w: the record's pixel box meets warp w's pixel block
+    uint8_t list[kMaxWarps][kBatch];   // per warp: the batch entries it must visit, in order
 };
+static_assert(kBatch <= 256, "batch entries are stored as bytes");
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Compacts the entries k < cnt of the staged batch whose mask has this warp's
+// bit (and, when `limit` is given, lie before it) into the warp's list, in
+// ascending order; returns their number. Called by all 32 lanes of the warp.
+__device__ __forceinline__ int build_warp_list(Stage& st, int cnt, uint32_t base, uint32_t limit) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t wbit = 1u << w, lt = lanemask_lt();
+    int nk = 0;
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
+        const int k = c0 + lane;
+        const bool hit = k < cnt && (st.mask[k] & wbit) && base + (uint32_t)k < limit;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, hit);
+        if (hit) st.list[w][nk + __popc(bal & lt)] = (uint8_t)k;
+        nk += __popc(bal);
+    }
+    __syncwarp();
+    return nk;
+}
 __device__ __forceinline__ Stage& stage() {
     __shared__ Stage st;
     return st;
@@ -220,9 +248,10 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
         }
         __syncthreads();
         const int cnt = min((uint32_t)kBatch, rg.y - bs);
-        const uint32_t wbit = 1u << (threadIdx.x >> 5);
-        for (int k = 0; k < cnt && nlive > 0; ++k) {
-            if (!(st.mask[k] & wbit)) continue;
+        const int nk = build_warp_list(st, cnt, 0u, 0xFFFFFFFFu);
+        const uint8_t* wl = st.list[threadIdx.x >> 5];
+        for (int i = 0; i < nk && nlive > 0; ++i) {
+            const int k = wl[i];
             const float4 a = s0[k];
             const float dx = g.fx - a.x;
             if (fabsf(dx) > a.z) continue;
@@ -296,6 +325,7 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
     if (lane == 0) atomicMax(&smax, wm);
     __syncthreads();
     const uint32_t end = smax;
+    const uint32_t warp_end = wm;
     for (uint32_t be = end; be > rg.x;) {
         const uint32_t bs = be - rg.x > (uint32_t)kBatch ? be - kBatch : rg.x;
         __syncthreads();
@@ -309,9 +339,10 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
             }
         }
         __syncthreads();
-        const uint32_t wbit = 1u << (threadIdx.x >> 5);
-        for (int k = (int)(be - bs) - 1; k >= 0; --k) {
-            if (!(st.mask[k] & wbit)) continue;
+        const int nk = build_warp_list(st, (int)(be - bs), bs, warp_end);
+        const uint8_t* wl = st.list[threadIdx.x >> 5];
+        for (int i = nk - 1; i >= 0; --i) {
+            const int k = wl[i];
             const uint32_t pos = bs + k;
             const float4 a = s0[k];
             const float dx = g.fx - a.x;

@@ -46,14 +46,16 @@ def canonical_targets(params: torch.Tensor) -> torch.Tensor:
 def run_stream(gm: GaussianMap, cams: Sequence, targets: torch.Tensor, points: Sequence[torch.Tensor],
                window: int = 8, iters: int = 100, insert: bool = True, densify: bool = True,
                collect: bool = False, track_psnr: str = "", mlp: Optional[MLP] = None,
-               flush: Optional[torch.Tensor] = None) -> dict:
+               flush: Optional[torch.Tensor] = None, clarity: bool = False) -> dict:
     """Run the mapping stream. ``targets`` [F, 3, H, W] and each ``points[j]`` [k, 3] live on the
     device. With ``mlp`` the learned initialiser initialises inserted Gaussians.
 
     ``track_psnr``: "" (none), "final" (the newest keyframe's PSNR after its last iteration,
     computed outside the timed region) or "curve" (after every iteration). Mapping time is
     taken with CUDA events around every iteration (PSNR kernels and the optional L2 ``flush``
-    write run between the brackets); insertion and densification are timed apart.
+    write run between the brackets); insertion and densification are timed apart. With
+    ``clarity`` the newest keyframe's dominated pixels are counted before each densification
+    (the Eq. 9 split mask, active when the map's clarity_sigma > 0).
 
     Returns statistics: Gaussians after each keyframe, inserted per keyframe, per-keyframe
     mapping ms, insertion and densification ms, PSNR ("psnr": [F] or [F, iters]), and (with
@@ -113,6 +115,8 @@ def run_stream(gm: GaussianMap, cams: Sequence, targets: torch.Tensor, points: S
                 ys.append(canonical_targets(gm.params()[:, n0:n0 + k]))
             d0 = ev()
             if densify:
+                if clarity:
+                    gm.count_dominant([cams[j]])
                 gm.densify()
             ev_den.append((d0, ev()))
             n_gauss.append(gm.n)

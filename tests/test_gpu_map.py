@@ -128,3 +128,69 @@ def test_densify_matches_oracle():
     np.testing.assert_array_equal(got[6:14, n_keep:], newP[6:14, n_keep:].astype(np.float32))
     # statistics are reset: a second densify splits nothing
     assert gm.densify(cuda(np.zeros((gm.n, 2, 3), np.float32))) == 0
+
+
+def test_dominance_counts_and_clarity_split_match_oracle():
+    """Eq. 8-9: per-Gaussian dominated-pixel counts from the kernel's argmax render against the
+    oracle's. A pixel whose two largest blend weights lie within 1e-4 of each other may go either
+    way in float32; each such pixel can move one count between two Gaussians."""
+    p, cam = frustum_scene(n=2000, seed=5)
+    p64 = p.astype(np.float64)
+    ref = O.render(p64, cam)
+    ora = O.dominance_counts([ref["argmax"]], 2000)
+    n_tie = int((ref["argmax_gap"] < 1e-4).sum())
+    # the counts live in the context; they are read through a split with only the clarity
+    # rule on, at a sigma in a wide gap of the oracle's counts
+    srt = np.unique(ora[ora > 0])
+    gaps = np.diff(srt)
+    lo = int(0.6 * len(srt))
+    i = lo + int(np.argmax(gaps[lo:]))
+    assert gaps[i] > 2 * n_tie + 1
+    sigma = float(srt[i]) + 0.5 * float(gaps[i])
+    gm2 = new_map(4000, split_thresh=1e30, clarity_sigma=sigma)
+    gm2.set_params(cuda(p))
+    gm2.count_dominant([cam])
+    z = np.random.default_rng(6).normal(size=(2000, 2, 3)).astype(np.float32)
+    n_split = gm2.densify(cuda(z))
+    newP, _, _, mask = O.split(p64, p64 * 0, p64 * 0, np.zeros(2000), np.zeros(2000), z.astype(np.float64),
+                               O.Config(split_thresh=1e30, clarity_sigma=sigma), dominant=ora)
+    assert n_split == int(mask.sum()) > 0
+    got = gm2.params().cpu().numpy()
+    np.testing.assert_array_equal(got[:, :2000 - n_split], p[:, ~mask])
+    np.testing.assert_allclose(got[0:6, 2000 - n_split:], newP[0:6, 2000 - n_split:], rtol=0, atol=1e-6)
+    # counting twice doubles the counts: the same sigma now splits at least as many
+    gm3 = new_map(4000, split_thresh=1e30, clarity_sigma=sigma)
+    gm3.set_params(cuda(p))
+    gm3.count_dominant([cam, cam])
+    assert gm3.densify(cuda(z)) >= n_split
+
+
+def test_distance_insertion_matches_oracle():
+    """Eq. 7 with the text's reading: insert iff the nearest existing mean is farther than tau.
+    Points whose distance lies within 1e-5 of tau are not placed; the decision is then exact."""
+    p, cam = frustum_scene(n=3000, seed=7)
+    image = random_target(160, 120, seed=8)[0]
+    rng = np.random.default_rng(9)
+    tau = 0.05
+    near = p[0:3, rng.choice(3000, 80, replace=False)].T + rng.normal(0, 0.01, size=(80, 3))
+    far = np.stack([rng.uniform(-2, 2, 80), rng.uniform(-1.5, 1.5, 80), rng.uniform(1, 5, 80)], 1)
+    pts = np.concatenate([near, far]).astype(np.float32)
+    mask, d = O.distance_insertion_mask(pts.astype(np.float64), p[0:3].T.astype(np.float64), O.Config(insert_tau=tau))
+    ok = np.abs(d - tau) > 1e-5
+    pts = pts[ok]
+    mask = mask[ok]
+    assert mask.any() and not mask.all()
+    gm = new_map(4000, insert_tau=tau)
+    gm.set_params(cuda(p))
+    n_ins, got_mask = gm.insert(cam, cuda(image), cuda(pts), return_mask=True)
+    np.testing.assert_array_equal(got_mask.cpu().numpy(), mask)
+    assert n_ins == int(mask.sum()) and gm.n == 3000 + n_ins
+    _, pixels, _ = O.insertion_mask(pts.astype(np.float64), cam, np.ones((120, 160)))
+    ref = O.plain_init(pts[mask].astype(np.float64), pixels[mask], image, p[0:3].T.astype(np.float64))
+    got = gm.params().cpu().numpy()[:, 3000:]
+    np.testing.assert_array_equal(got[0:3], pts[mask].T)
+    np.testing.assert_allclose(got[3:6], ref[3:6], rtol=0, atol=2e-6)
+    np.testing.assert_array_equal(got[11:14], ref[11:14].astype(np.float32))
+    # into an empty map every point goes in
+    ge = new_map(4000, insert_tau=tau)
+    assert ge.insert(cam, cuda(image), cuda(pts)) == len(pts)

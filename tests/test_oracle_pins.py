@@ -491,6 +491,65 @@ def test_split_threshold_and_order():
     np.testing.assert_array_equal(newP[0:3, 2:], P[0:3, [0, 0, 2, 2]])  # then children, z = 0
 
 
+def test_dominance_count_single_gaussian_closed_form():
+    """One isotropic Gaussian on the axis dominates exactly the pixels where it blends:
+    |dx|, |dy| <= r and o exp(-(dx^2 + dy^2) / (2 sigma^2)) >= 1/255, sigma^2 = (f s/z)^2 + 0.3."""
+    f, z, s, o = 100.0, 2.0, 0.05, 0.5
+    cam = _axis_cam(f)
+    p = _params([[0, 0, z]], [[math.log(s)] * 3], [[1, 0, 0, 0]], [_logit(o)], [[0.5, 0.5, 0.5]])
+    out = O.render(p, cam)
+    cnt = O.dominance_counts([out["argmax"]], 1)
+    sig2 = (f * s / z) ** 2 + 0.3
+    r = 8
+    expect = sum(1 for dx in range(-r, r + 1) for dy in range(-r, r + 1)
+                 if o * math.exp(-(dx * dx + dy * dy) / (2 * sig2)) >= 1 / 255)
+    # blending needs dx^2 + dy^2 <= 2 sigma^2 ln(255 o) = 63.5: the 193 lattice points of that disc
+    assert cnt[0] == expect == sum(1 for dx in range(-8, 9) for dy in range(-8, 9) if dx * dx + dy * dy <= 63) == 193
+
+
+def test_dominance_front_opaque_layer_takes_every_pixel():
+    """A front layer with alpha 0.99 at every pixel of the back layer's footprint outweighs it
+    (0.99 against at most 0.01 * 0.99); pixels only the back layer covers stay its own."""
+    cam = _axis_cam(100.0)
+    p = _params([[0, 0, 1.0], [0, 0, 2.0]], [[math.log(2.0)] * 3, [math.log(0.05)] * 3], [[1, 0, 0, 0]] * 2,
+                [_logit(0.9999), _logit(0.9)], [[1, 0, 0], [0, 1, 0]])
+    out = O.render(p, cam)
+    a = out["argmax"]
+    assert (a == 0).all()
+    cnt = O.dominance_counts([a, a], 2)
+    assert cnt[0] == 2 * 64 * 64 and cnt[1] == 0
+    assert list(O.dominance_counts([np.full((4, 4), -1)], 3)) == [0, 0, 0]
+
+
+def test_split_with_clarity_mask_is_union():
+    rng = np.random.default_rng(3)
+    p = rng.normal(size=(14, 6))
+    z = rng.normal(size=(6, 2, 3))
+    gs, gc = np.array([3e-4, 0, 0, 1e-4, 0, 0]), np.ones(6)
+    dom = np.array([0, 50, 10, 0, 11, 0])
+    cfg = O.Config(clarity_sigma=10.0)
+    _, _, _, mask = O.split(p, p * 0, p * 0, gs, gc, z, cfg, dominant=dom)
+    assert list(mask) == [True, True, False, False, True, False]
+    _, _, _, off = O.split(p, p * 0, p * 0, gs, gc, z, O.Config(), dominant=dom)   # sigma 0: gradient rule only
+    assert list(off) == [True, False, False, False, False, False]
+
+
+def test_distance_insertion_matches_kdtree():
+    spatial = pytest.importorskip("scipy.spatial")
+    rng = np.random.default_rng(8)
+    means = rng.uniform(-1, 1, size=(3000, 3))
+    pts = rng.uniform(-1.2, 1.2, size=(400, 3))
+    pts[:5] = means[:5]                                 # exactly on a mean: distance 0, skipped
+    cfg = O.Config(insert_tau=0.06)
+    mask, d = O.distance_insertion_mask(pts, means, cfg)
+    dk, _ = spatial.cKDTree(means).query(pts)
+    np.testing.assert_allclose(d, dk, rtol=1e-12, atol=1e-15)
+    np.testing.assert_array_equal(mask, dk > 0.06)
+    assert not mask[:5].any() and mask.any() and not mask.all()
+    m0, d0 = O.distance_insertion_mask(pts, np.zeros((0, 3)), cfg)
+    assert m0.all() and np.isinf(d0).all()
+
+
 def test_init_map_knn_excludes_self():
     X = np.array([[0, 0, 0], [0.1, 0, 0], [0, 0.2, 0], [0, 0, 0.3], [5, 5, 5.0]])
     out = O.init_map(X, np.full((5, 3), 0.5))
@@ -601,3 +660,71 @@ def test_mlp_features_layout():
     # point 1 projects to (-10.5 + 10 -> pixel 0 after clamping), y 5 - 10 = -5 -> 0: borders clamp
     assert np.all(f[1, 0:75:3] >= 0) and f[1, 0] == 0 and f[1, 1] == 0
     np.testing.assert_allclose(f[0, 75:80], [2.0, 0.0, 0.0, 2.0, 0.0])
+
+
+# ------------------------------------------------------------------ SSIM term (Eq. 10 L_SSIM)
+
+
+def test_ssim_identity_and_constant_closed_form():
+    rng = np.random.default_rng(4)
+    x = torch.tensor(rng.uniform(size=(3, 24, 20)))
+    np.testing.assert_allclose(O.ssim_map(x, x).numpy(), 1.0, rtol=0, atol=1e-12)
+    # constant images c1, c2 away from the border (window fully inside): variances vanish
+    a, b = torch.full((3, 30, 30), 0.3, dtype=torch.float64), torch.full((3, 30, 30), 0.7, dtype=torch.float64)
+    m = O.ssim_map(a, b).numpy()[:, 5:-5, 5:-5]
+    C1 = 0.01 ** 2
+    np.testing.assert_allclose(m, (2 * 0.3 * 0.7 + C1) / (0.3 ** 2 + 0.7 ** 2 + C1), rtol=1e-12)
+
+
+def test_ssim_matches_scipy_gaussian_filter():
+    """The windowed statistics are scipy's Gaussian filter (sigma 1.5, radius 5, zero padding)."""
+    nd = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(5)
+    x, y = rng.uniform(size=(3, 26, 31)), rng.uniform(size=(3, 26, 31))
+
+    def blur(z):
+        return np.stack([nd.gaussian_filter(c, 1.5, truncate=5 / 1.5, mode="constant", cval=0.0) for c in z])
+    mx, my = blur(x), blur(y)
+    sxx, syy, sxy = blur(x * x) - mx * mx, blur(y * y) - my * my, blur(x * y) - mx * my
+    C1, C2 = 0.01 ** 2, 0.03 ** 2
+    ref = (2 * mx * my + C1) * (2 * sxy + C2) / ((mx * mx + my * my + C1) * (sxx + syy + C2))
+    np.testing.assert_allclose(O.ssim_map(torch.tensor(x), torch.tensor(y)).numpy(), ref, rtol=1e-10, atol=1e-12)
+
+
+def test_color_loss_weights():
+    rng = np.random.default_rng(6)
+    x, y = torch.tensor(rng.uniform(size=(3, 16, 16))), torch.tensor(rng.uniform(size=(3, 16, 16)))
+    l1 = float((x - y).abs().mean())
+    s = float(O.ssim_map(x, y).mean())
+    assert float(O.color_loss(x, y)) == pytest.approx(l1, rel=1e-15)
+    assert float(O.color_loss(x, y, O.Config(lambda_photo=0.2))) == pytest.approx(0.8 * l1 + 0.2 * (1 - s), rel=1e-14)
+
+
+@pytest.mark.parametrize("seed,n", [(3, 2), (4, 4)])
+def test_gradient_finite_differences_with_ssim(seed, n):
+    """The whole-image SSIM path of the oracle's gradient against central differences."""
+    p, cam = frustum_scene(n=n, width=16, height=16, fx=16.0, fy=16.0, cx=8.0, cy=8.0, seed=seed,
+                           logscale_mean=-1.5)
+    p = p.astype(np.float64)
+    tg = np.random.default_rng(seed).uniform(size=(1, 3, 16, 16))
+    cfg = O.Config(lambda_photo=0.2)
+    res = O.loss_and_grads(p, [cam], tg, cfg)
+    g = res["grad"]
+    base = O.decision_signature(p, [cam])
+    checked = 0
+    for i in range(14):
+        for j in range(n):
+            h = 1e-5 * max(1.0, abs(p[i, j]))
+            pp, pm = p.copy(), p.copy()
+            pp[i, j] += h
+            pm[i, j] -= h
+            if O.decision_signature(pp, [cam]) != base or O.decision_signature(pm, [cam]) != base:
+                continue
+            fd = (O.loss_value(pp, [cam], tg, cfg) - O.loss_value(pm, [cam], tg, cfg)) / (2 * h)
+            assert abs(fd - g[i, j]) <= 1e-5 * abs(g[i, j]) + 100 * np.finfo(float).eps * abs(res["loss"]) / h, \
+                (i, j, fd, g[i, j])
+            checked += 1
+    assert checked >= 0.8 * 14 * n
+    # the SSIM term changes the gradient (it is not the L1 gradient)
+    g1 = O.loss_and_grads(p, [cam], tg)["grad"]
+    assert np.abs(g - g1).max() > 1e-3 * np.abs(g1).max()
