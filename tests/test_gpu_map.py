@@ -159,7 +159,7 @@ def test_dominance_counts_and_clarity_split_match_oracle():
     np.testing.assert_array_equal(got[:, :2000 - n_split], p[:, ~mask])
     np.testing.assert_allclose(got[0:6, 2000 - n_split:], newP[0:6, 2000 - n_split:], rtol=0, atol=1e-6)
     # counting twice doubles the counts: the same sigma now splits at least as many
-    gm3 = new_map(4000, split_thresh=1e30, clarity_sigma=sigma)
+    gm3 = new_map(4000, views=2, split_thresh=1e30, clarity_sigma=sigma)
     gm3.set_params(cuda(p))
     gm3.count_dominant([cam, cam])
     assert gm3.densify(cuda(z)) >= n_split
