@@ -333,7 +333,7 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         if (e != cudaSuccess) { code = fail(c, GS_ERR_CUDA, "cudaSetDevice", e); break; }
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
         if (c->num_sms <= 0) c->num_sms = 1;
-        c->sort_blocks = c->num_sms * 2;
+        c->sort_blocks = c->num_sms * 4;
         c->n_partials = 2 * c->num_sms * 2;
         const size_t cap = (size_t)c->cap, V = (size_t)cfg->max_views;
         const size_t maxpix = (size_t)cfg->max_width * cfg->max_height;
@@ -348,6 +348,7 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         ok = ok && dalloc(&c->dens_sum, cap) == cudaSuccess;
         ok = ok && dalloc(&c->dens_cnt, cap) == cudaSuccess;
         ok = ok && dalloc(&c->dom_cnt, cap) == cudaSuccess;
+        ok = ok && dalloc(&c->adam_pw, 2) == cudaSuccess;
         ok = ok && dalloc(&c->dcam, V) == cudaSuccess;
         ok = ok && dalloc(&c->rec, 3 * V * cap) == cudaSuccess;
         ok = ok && dalloc(&c->tiles_touched, V * cap) == cudaSuccess;
@@ -382,6 +383,8 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         if (e == cudaSuccess) e = cudaMemset(c->dens_sum, 0, sizeof(float) * cap);
         if (e == cudaSuccess) e = cudaMemset(c->dens_cnt, 0, sizeof(float) * cap);
         if (e == cudaSuccess) e = cudaMemset(c->dom_cnt, 0, sizeof(uint32_t) * cap);
+        const double pw1[2] = {1.0, 1.0};
+        if (e == cudaSuccess) e = cudaMemcpy(c->adam_pw, pw1, sizeof(pw1), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) { code = fail(c, GS_ERR_CUDA, "initialisation", e); break; }
     } while (0);
@@ -402,7 +405,7 @@ void gs_destroy(gs_ctx* c) {
         cudaEventDestroy(r.b);
     }
     for (auto e : c->tpool) cudaEventDestroy(e);
-    void* ptrs[] = {c->params, c->grads, c->adam_m, c->adam_v, c->dens_sum, c->dens_cnt, c->dom_cnt, c->dcam, c->rec,
+    void* ptrs[] = {c->params, c->grads, c->adam_m, c->adam_v, c->dens_sum, c->dens_cnt, c->dom_cnt, c->adam_pw, c->dcam, c->rec,
                     c->tiles_touched, c->depth, c->dkey[0], c->dkey[1], c->dval[0], c->dval[1], c->offsets, c->ranges,
                     c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->dcount, c->partials, c->fpart,
                     c->own_rgb};
@@ -440,6 +443,10 @@ int gs_set_params(gs_ctx* c, const float* params_dev, int n, void* stream) {
     CK(cudaMemsetAsync(c->dens_cnt, 0, sizeof(float) * c->cap, s));
     CK(cudaMemsetAsync(c->dom_cnt, 0, sizeof(uint32_t) * c->cap, s));
     CK(cudaMemsetAsync(c->dcount + 4, 0, sizeof(uint32_t), s));
+    {
+        static const double pw1[2] = {1.0, 1.0};
+        CK(cudaMemcpyAsync(c->adam_pw, pw1, sizeof(pw1), cudaMemcpyHostToDevice, s));
+    }
     c->n = n;
     c->adam_t = 0;
     c->n_views = 0;

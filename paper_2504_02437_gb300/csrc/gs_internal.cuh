@@ -63,6 +63,7 @@ struct gs_ctx {
     int n = 0;                  // Gaussians in the map
     int cap = 0;                // capacity (Gaussians)
     int adam_t = 0;             // Adam steps taken
+    double* adam_pw = nullptr;  // device {beta1^t, beta2^t} after t steps
     std::string err;
 
     // map state, [14][cap] planar

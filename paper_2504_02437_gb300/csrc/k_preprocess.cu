@@ -29,6 +29,67 @@ struct Proj {
     float A, B, C, det;    // dilated 2D covariance
 };
 
+// Float-float ("double-float") arithmetic: a value is hi + lo with |lo| <=
+// ulp(hi)/2, about 48 significant bits. Error-free transformations: TwoSum
+// (Knuth, TAOCP vol. 2, 4.2.2) and TwoProduct through a fused multiply-add
+// (Dekker 1971; with FMA as in Ogita, Rump and Oishi 2005). The intrinsics
+// keep the compiler from contracting or reassociating the steps.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ FF quick_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+    const FF s = two_sum(x.hi, y.hi);
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+// r0 m0 + r1 m1 + r2 m2 + t of float32 inputs
+__device__ __forceinline__ FF ff_dot3_add(float r0, float m0, float r1, float m1, float r2, float m2, float t) {
+    FF acc = two_prod(r0, m0);
+    acc = ff_add(acc, two_prod(r1, m1));
+    acc = ff_add(acc, two_prod(r2, m2));
+    return ff_add(acc, FF{t, 0.f});
+}
+__device__ __forceinline__ FF ff_div(FF a, FF b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const FF p = two_prod(q1, b.hi);
+    // remainder a - q1 b, to first order
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p.hi), p.lo), __fsub_rn(a.lo, __fmul_rn(q1, b.lo)));
+    return quick_two_sum(q1, __fdiv_rn(r, b.hi));
+}
+// f a + c
+__device__ __forceinline__ FF ff_scale_add(FF a, float f, float c) {
+    FF p = two_prod(a.hi, f);
+    p = quick_two_sum(p.hi, __fmaf_rn(a.lo, f, p.lo));
+    return ff_add(p, FF{c, 0.f});
+}
+// floor and fraction of hi + lo: returns the integer part, writes the fraction in [0, 1)
+__device__ __forceinline__ float ff_floor_frac(FF a, float& frac) {
+    float fl = floorf(a.hi);
+    float f = __fadd_rn(__fsub_rn(a.hi, fl), a.lo);   // a.hi - fl is exact
+    if (f < 0.f) {
+        fl -= 1.f;
+        f = __fadd_rn(f, 1.f);
+    } else if (f >= 1.f) {
+        fl += 1.f;
+        f = __fsub_rn(f, 1.f);
+    }
+    frac = fminf(fmaxf(f, 0.f), 0x1.fffffep-1f);
+    return fl;
+}
+
 __device__ __forceinline__ void load_params(const float* __restrict__ P, int cap, int i, float p[kParamRows]) {
 #pragma unroll
     for (int r = 0; r < kParamRows; ++r) p[r] = __ldg(P + (size_t)r * cap + i);
@@ -110,34 +171,29 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ P,
     shape_of(p, g);
     Proj o;
     project_one(p, g, cam, kc.dilation, o);
-    // Screen mean and depth in float64 (the covariance stays float32): the
+    // Screen mean and depth in float-float (the covariance stays float32): the
     // compositing subtracts u from pixel coordinates, and the rounding of u in
     // float32 (about 1e-4 px at 1000 px) would dominate the error of the
     // cancelling sums of the mean gradient.
-    const double mx = p[0], my = p[1], mz = p[2];
-    const double txd = fma((double)cam.R[0], mx, fma((double)cam.R[1], my, fma((double)cam.R[2], mz, (double)cam.t[0])));
-    const double tyd = fma((double)cam.R[3], mx, fma((double)cam.R[4], my, fma((double)cam.R[5], mz, (double)cam.t[1])));
-    const double tzd = fma((double)cam.R[6], mx, fma((double)cam.R[7], my, fma((double)cam.R[8], mz, (double)cam.t[2])));
-    const double izd = 1.0 / tzd;
-    const double ud = (double)cam.fx * txd * izd + (double)cam.cx;
-    const double vd = (double)cam.fy * tyd * izd + (double)cam.cy;
-    const float tz32 = (float)tzd;
-    bool valid = (tzd > (double)kc.near_z) && (o.det > 0.f);
+    const FF tzf = ff_dot3_add(cam.R[6], p[0], cam.R[7], p[1], cam.R[8], p[2], cam.t[2]);
+    const FF txf = ff_dot3_add(cam.R[0], p[0], cam.R[1], p[1], cam.R[2], p[2], cam.t[0]);
+    const FF tyf = ff_dot3_add(cam.R[3], p[0], cam.R[4], p[1], cam.R[5], p[2], cam.t[1]);
+    const float tz32 = tzf.hi;
+    bool valid = (tzf.hi > kc.near_z || (tzf.hi == kc.near_z && tzf.lo > 0.f)) && (o.det > 0.f);
+    const FF izx = ff_div(txf, tzf), izy = ff_div(tyf, tzf);
+    const FF uf2 = ff_scale_add(izx, cam.fx, cam.cx), vf2 = ff_scale_add(izy, cam.fy, cam.cy);
     float idet = 1.0f / o.det;
     float ca = o.C * idet, cb = -o.B * idet, cc = o.A * idet;
     float mid = 0.5f * (o.A + o.C);
     float lam = mid + sqrtf(fmaxf(kc.lambda_floor, mid * mid - o.det));
     float r = ceilf(kc.radius_sigma * sqrtf(lam));
     // screen positions beyond +-2^23 px or radii beyond 2^22 px are culled
-    valid = valid && fabs(ud) < 8388608.0 && fabs(vd) < 8388608.0 && r < 4194304.f;
+    valid = valid && fabsf(uf2.hi) < 8388608.f && fabsf(vf2.hi) < 8388608.f && r < 4194304.f;
     float ui = 0.f, uf = 0.f, vi = 0.f, vf = 0.f;
     uint32_t ntiles = 0;
     if (valid) {
-        const double fu = floor(ud), fv = floor(vd);
-        ui = (float)fu;
-        vi = (float)fv;
-        uf = fminf((float)(ud - fu), 0x1.fffffep-1f);
-        vf = fminf((float)(vd - fv), 0x1.fffffep-1f);
+        ui = ff_floor_frac(uf2, uf);
+        vi = ff_floor_frac(vf2, vf);
         int x0, x1, y0, y1;
         if (pixel_box(ui, uf, vi, vf, r, cam.width, cam.height, x0, x1, y0, y1))
             ntiles = (uint32_t)((x1 / tile - x0 / tile + 1) * (y1 / tile - y0 / tile + 1));

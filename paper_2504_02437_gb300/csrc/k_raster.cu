@@ -292,7 +292,10 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
 // back to front from the block's largest last-blended entry, recovering
 // T_i = T_{i+1} / (1 - alpha_i) from the final T, and accumulates the
 // gradients w.r.t. each Gaussian's screen quantities (warp sum, then one
-// 9-lane atomic per Gaussian and warp).
+// 9-lane atomic per Gaussian and warp; when a single lane blended, that lane
+// adds its 9 values itself with two float4 atomics and one scalar). Each
+// warp visits only the batch entries its compacted list holds, which stop at
+// the warp's largest last-blended entry.
 template <int TILE, int PPT>
 __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uint32_t* __restrict__ pval,
                                          const float4* __restrict__ rec, const DevConst& kc, float (&T)[PPT],
@@ -388,7 +391,18 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
                     }
                 }
             }
-            if (!__any_sync(0xFFFFFFFFu, any)) continue;
+            const uint32_t who = __ballot_sync(0xFFFFFFFFu, any);
+            if (who == 0u) continue;
+            if ((who & (who - 1u)) == 0u) {
+                // a single lane blended this Gaussian: it adds its own values (no warp sum)
+                if (any) {
+                    float* gp = grad2d + (size_t)sid[k] * kGrad2dStride;
+                    atomicAdd(reinterpret_cast<float4*>(gp), make_float4(acc[0], acc[1], acc[2], acc[3]));
+                    atomicAdd(reinterpret_cast<float4*>(gp + 4), make_float4(acc[4], acc[5], acc[6], acc[7]));
+                    atomicAdd(gp + 8, acc[8]);
+                }
+                continue;
+            }
             int idx;
             const float v = warp_sum9(acc, lane, idx);
             if (idx >= 0) atomicAdd(grad2d + (size_t)sid[k] * kGrad2dStride + idx, v);

@@ -40,27 +40,37 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-// Histogram of one digit over each block's slice: hist[d * G + b].
+// Histogram of one digit over each block's slice: hist[d * G + b]. Each warp
+// counts into its own shared sub-histogram (shared-memory atomics); every
+// thread has four keys in flight per round.
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys,
                                                              const uint32_t* __restrict__ n_dev, uint32_t n_max,
                                                              int shift, int nbits, uint32_t* __restrict__ hist) {
-    __shared__ uint32_t h[256];
-    const int G = gridDim.x, b = blockIdx.x;
+    __shared__ uint32_t h[kSortWarps][256];
+    const int G = gridDim.x, b = blockIdx.x, w = threadIdx.x >> 5;
     const uint32_t mask = (1u << nbits) - 1u;
-    for (int d = threadIdx.x; d < 256; d += kSortThreads) h[d] = 0;
+    for (int d = threadIdx.x; d < kSortWarps * 256; d += kSortThreads) (&h[0][0])[d] = 0;
     __syncthreads();
     uint32_t n = umin(*n_dev, n_max), begin, end;
     slice_of(n, G, b, begin, end);
-    const int lane = threadIdx.x & 31;
-    for (uint32_t base = begin + (threadIdx.x & ~31u); base < end; base += kSortThreads) {
-        uint32_t i = base + lane;
-        bool ok = i < end;
-        uint32_t d = ok ? (keys[i] >> shift) & mask : 0xFFFFFFFFu;
-        uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-        if (ok && (__ffs(peers) - 1) == lane) atomicAdd(&h[d], (uint32_t)__popc(peers));
+    for (uint32_t base = begin + threadIdx.x; base < end; base += 4 * kSortThreads) {
+        uint32_t k[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t i = base + u * kSortThreads;
+            k[u] = i < end ? keys[i] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (base + u * kSortThreads < end) atomicAdd(&h[w][(k[u] >> shift) & mask], 1u);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d <= (int)mask; d += kSortThreads) hist[(size_t)d * G + b] = h[d];
+    for (int d = threadIdx.x; d <= (int)mask; d += kSortThreads) {
+        uint32_t t = 0;
+#pragma unroll
+        for (int ww = 0; ww < kSortWarps; ++ww) t += h[ww][d];
+        hist[(size_t)d * G + b] = t;
+    }
 }
 
 // In-place exclusive scan of `len` counters with one block of 1024 threads,
@@ -324,8 +334,8 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ pke
 cudaError_t radix_sort_pairs(gs_ctx* c, uint32_t** keys, uint32_t** vals, const uint32_t* n_dev, uint32_t n_max,
                              uint32_t n_hint, int bits, int* out_buf, cudaStream_t s) {
     int cur = 0;
-    // about 4096 elements per block (each block owns one contiguous slice)
-    const int G = (int)std::max<uint32_t>(1u, std::min<uint32_t>((uint32_t)c->sort_blocks, (n_hint + 4095u) / 4096u));
+    // about 2048 elements (one scatter round) per block, each block owning one contiguous slice
+    const int G = (int)std::max<uint32_t>(1u, std::min<uint32_t>((uint32_t)c->sort_blocks, (n_hint + 2047u) / 2048u));
     for (int shift = 0; shift < bits; shift += 8) {
         int nb = bits - shift < 8 ? bits - shift : 8;
         c->launches += 3;

@@ -101,48 +101,64 @@ struct AdamArgs {
     float b1, b2, eps;
 };
 
-// Bias corrections of the next Adam step, from the device-side step counter
-// (so that a captured graph replays correctly): st[4] = completed steps,
-// st[1] = pair-buffer overflow flag of this iteration (step skipped),
-// bc = {1 - beta1^t, 1 - beta2^t, skip}.
-__global__ void k_adam_prep(uint32_t* __restrict__ st, float b1, float b2, float* __restrict__ bc) {
-    const bool skip = st[1] != 0u;
-    const double t = (double)st[4] + 1.0;
-    bc[0] = (float)(1.0 - pow((double)b1, t));
-    bc[1] = (float)(1.0 - pow((double)b2, t));
-    bc[2] = skip ? 1.f : 0.f;
-    if (!skip) st[4] += 1u;
-}
-
 // One Adam step; each thread updates 4 consecutive parameters of one row.
+// The bias corrections come from device state, so that a captured graph
+// replays correctly: pw = {beta1^t, beta2^t} (float64 running products, no
+// pow) after t completed steps, st[4] = t, st[1] = pair-buffer overflow flag
+// of this iteration (the step is skipped), st[2] = ticket of the CTAs done.
+// Every CTA reads pw before it takes its ticket, and the last CTA advances
+// pw and t, so all CTAs of one launch use the same t + 1.
 __global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, const float* __restrict__ G,
                                               float* __restrict__ M, float* __restrict__ V, int n, int cap,
-                                              AdamArgs a, const float* __restrict__ bc) {
+                                              AdamArgs a, uint32_t* __restrict__ st, double* __restrict__ pw) {
+    __shared__ float sbc[3];
+    __shared__ double spw[2];
+    if (threadIdx.x == 0) {
+        const double p1 = pw[0] * (double)a.b1, p2 = pw[1] * (double)a.b2;
+        spw[0] = p1;
+        spw[1] = p2;
+        sbc[0] = (float)(1.0 - p1);
+        sbc[1] = (float)(1.0 - p2);
+        sbc[2] = st[1] != 0u ? 1.f : 0.f;
+    }
+    __syncthreads();
     const int j = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int row = blockIdx.y;
-    if (j >= n || bc[2] != 0.f) return;
-    const float bc1 = bc[0], bc2 = bc[1], lr = a.lr[row];
-    const size_t k = (size_t)row * cap + j;
-    auto upd = [&](float& p, float g, float& m, float& v) {
-        m = a.b1 * m + (1.f - a.b1) * g;
-        v = a.b2 * v + (1.f - a.b2) * g * g;
-        const float mh = m / bc1, vh = v / bc2;
-        p -= lr * mh / (sqrtf(vh) + a.eps);
-    };
-    if (j + 3 < n) {
-        float4 p = *reinterpret_cast<float4*>(P + k);
-        const float4 g = *reinterpret_cast<const float4*>(G + k);
-        float4 m = *reinterpret_cast<float4*>(M + k);
-        float4 v = *reinterpret_cast<float4*>(V + k);
-        upd(p.x, g.x, m.x, v.x);
-        upd(p.y, g.y, m.y, v.y);
-        upd(p.z, g.z, m.z, v.z);
-        upd(p.w, g.w, m.w, v.w);
-        *reinterpret_cast<float4*>(P + k) = p;
-        *reinterpret_cast<float4*>(M + k) = m;
-        *reinterpret_cast<float4*>(V + k) = v;
-    } else {
-        for (int e = 0; e < 4 && j + e < n; ++e) upd(P[k + e], G[k + e], M[k + e], V[k + e]);
+    if (j < n && sbc[2] == 0.f) {
+        const float bc1 = sbc[0], bc2 = sbc[1], lr = a.lr[row];
+        const size_t k = (size_t)row * cap + j;
+        auto upd = [&](float& p, float g, float& m, float& v) {
+            m = a.b1 * m + (1.f - a.b1) * g;
+            v = a.b2 * v + (1.f - a.b2) * g * g;
+            const float mh = m / bc1, vh = v / bc2;
+            p -= lr * mh / (sqrtf(vh) + a.eps);
+        };
+        if (j + 3 < n) {
+            float4 p = *reinterpret_cast<float4*>(P + k);
+            const float4 g = *reinterpret_cast<const float4*>(G + k);
+            float4 m = *reinterpret_cast<float4*>(M + k);
+            float4 v = *reinterpret_cast<float4*>(V + k);
+            upd(p.x, g.x, m.x, v.x);
+            upd(p.y, g.y, m.y, v.y);
+            upd(p.z, g.z, m.z, v.z);
+            upd(p.w, g.w, m.w, v.w);
+            *reinterpret_cast<float4*>(P + k) = p;
+            *reinterpret_cast<float4*>(M + k) = m;
+            *reinterpret_cast<float4*>(V + k) = v;
+        } else {
+            for (int e = 0; e < 4 && j + e < n; ++e) upd(P[k + e], G[k + e], M[k + e], V[k + e]);
+        }
+    }
+    if (threadIdx.x == 0) {
+        const uint32_t total = gridDim.x * gridDim.y;
+        if (atomicAdd(st + 2, 1u) == total - 1u) {
+            if (sbc[2] == 0.f) {
+                pw[0] = spw[0];
+                pw[1] = spw[1];
+                st[4] += 1u;
+            }
+            st[2] = 0u;
+        }
     }
 }
 
@@ -181,11 +197,9 @@ cudaError_t launch_adam(gs_ctx* c, cudaStream_t s) {
     a.b1 = c->cfg.beta1;
     a.b2 = c->cfg.beta2;
     a.eps = c->cfg.eps;
-    float* bc = c->partials + c->n_partials + 4;
-    c->launches += 2;
-    k_adam_prep<<<1, 1, 0, s>>>(c->dcount, c->cfg.beta1, c->cfg.beta2, bc);
+    ++c->launches;
     dim3 grid(((c->n + 3) / 4 + 255) / 256, kParamRows);
-    k_adam<<<grid, 256, 0, s>>>(c->params, c->grads, c->adam_m, c->adam_v, c->n, c->cap, a, bc);
+    k_adam<<<grid, 256, 0, s>>>(c->params, c->grads, c->adam_m, c->adam_v, c->n, c->cap, a, c->dcount, c->adam_pw);
     return cudaGetLastError();
 }
 

@@ -53,30 +53,35 @@ def test_densify_splits_in_stream():
 
 
 def test_learned_initialiser_reaches_plain_psnr_sooner():
-    """Full-size keyframes (640x480): an initialiser trained on one sequence's converged
-    Gaussians reaches, on a held-out sequence, the PSNR plain initialisation has after 100
-    iterations in fewer iterations on average."""
+    """Full-size keyframes (640x480), the learned-initialiser protocol at reduced size: the
+    MLP is trained on the converged Gaussians of two 60-keyframe plain streams, then a held-out
+    16-keyframe sequence is mapped twice (plain, learned); per keyframe, the learned stream
+    reaches the newest keyframe's PSNR that the plain stream has after 100 iterations in fewer
+    iterations on average. (From one map state with fresh Adam moments the two initialisers
+    end level after 100 iterations; the gain builds up over the stream.)"""
     from paper_2504_02437_gb300 import stream as S
     from paper_2504_02437_gb300.api import GaussianMap, MLP
     iters = 100
 
     def new():
         return GaussianMap(capacity=1_000_000, max_views=8, max_width=640, max_height=480)
-    cams, tg, pts = stream_sequence(0, 30)
-    gm = new()
-    st = S.run_stream(gm, cams, tg, pts, iters=iters, collect=True)
-    gm.close()
-    X, Y = st["features"], st["targets"]
-    assert X.shape[0] == sum(st["n_inserted"]) and Y.shape == (X.shape[0], 16)
+    X, Y = [], []
+    for seed in (0, 1):
+        cams, tg, pts = stream_sequence(seed, 60)
+        gm = new()
+        st = S.run_stream(gm, cams, tg, pts, iters=iters, collect=True)
+        gm.close()
+        assert st["features"].shape[0] == sum(st["n_inserted"]) and st["targets"].shape[1] == 16
+        X.append(st["features"])
+        Y.append(st["targets"])
     mlp = MLP(seed=0)
-    losses = S.train_mlp(mlp, X, Y, epochs=300, batch=1024)
+    losses = S.train_mlp(mlp, torch.cat(X), torch.cat(Y), epochs=300, batch=4096)
     assert losses[-1] < 0.5 * losses[0]
-    cams, tg, pts = stream_sequence(100, 12)
+    cams, tg, pts = stream_sequence(100, 16)
     curves = {}
     for name, m in (("plain", None), ("mlp", mlp)):
         gm = new()
         curves[name] = S.run_stream(gm, cams, tg, pts, iters=iters, track_psnr="curve", mlp=m)["psnr"][1:]
         gm.close()
-    goal = curves["plain"][:, -1]
-    k = S.iterations_to_reach(curves["mlp"], goal).numpy()
-    assert np.mean(np.minimum(k, iters)) <= 0.92 * iters, k
+    k = S.iterations_to_reach(curves["mlp"], curves["plain"][:, -1]).numpy()
+    assert np.mean(np.minimum(k, iters)) <= 0.9 * iters, k
