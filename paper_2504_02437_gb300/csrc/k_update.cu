@@ -1,4 +1,6 @@
 // Loss (Eq. 10-11, Section 3.2 "Map Optimization") and the Adam update.
+#include <algorithm>
+
 #include "gs_internal.cuh"
 
 namespace gs {
@@ -101,8 +103,8 @@ struct AdamArgs {
     float b1, b2, eps;
 };
 
-// One Adam step; each thread updates 4 consecutive parameters of one row.
-// The bias corrections come from device state, so that a captured graph
+// One Adam step over a persistent grid; each thread updates groups of 4
+// consecutive parameters of one row. The bias corrections come from device state, so that a captured graph
 // replays correctly: pw = {beta1^t, beta2^t} (float64 running products, no
 // pow) after t completed steps, st[4] = t, st[1] = pair-buffer overflow flag
 // of this iteration (the step is skipped), st[2] = ticket of the CTAs done.
@@ -122,36 +124,40 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, const float
         sbc[2] = st[1] != 0u ? 1.f : 0.f;
     }
     __syncthreads();
-    const int j = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int row = blockIdx.y;
-    if (j < n && sbc[2] == 0.f) {
-        const float bc1 = sbc[0], bc2 = sbc[1], lr = a.lr[row];
-        const size_t k = (size_t)row * cap + j;
-        auto upd = [&](float& p, float g, float& m, float& v) {
+    if (sbc[2] == 0.f) {
+        const float bc1 = sbc[0], bc2 = sbc[1];
+        auto upd = [&](float& p, float g, float& m, float& v, float lr) {
             m = a.b1 * m + (1.f - a.b1) * g;
             v = a.b2 * v + (1.f - a.b2) * g * g;
             const float mh = m / bc1, vh = v / bc2;
             p -= lr * mh / (sqrtf(vh) + a.eps);
         };
-        if (j + 3 < n) {
-            float4 p = *reinterpret_cast<float4*>(P + k);
-            const float4 g = *reinterpret_cast<const float4*>(G + k);
-            float4 m = *reinterpret_cast<float4*>(M + k);
-            float4 v = *reinterpret_cast<float4*>(V + k);
-            upd(p.x, g.x, m.x, v.x);
-            upd(p.y, g.y, m.y, v.y);
-            upd(p.z, g.z, m.z, v.z);
-            upd(p.w, g.w, m.w, v.w);
-            *reinterpret_cast<float4*>(P + k) = p;
-            *reinterpret_cast<float4*>(M + k) = m;
-            *reinterpret_cast<float4*>(V + k) = v;
-        } else {
-            for (int e = 0; e < 4 && j + e < n; ++e) upd(P[k + e], G[k + e], M[k + e], V[k + e]);
+        // grid-stride over the 14 rows x ceil(n / 4) groups of 4 parameters
+        const uint32_t nvec = (uint32_t)(n + 3) / 4u, total = nvec * (uint32_t)kParamRows;
+        for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+            const uint32_t row = idx / nvec, j = 4u * (idx - row * nvec);
+            const float lr = a.lr[row];
+            const size_t k = (size_t)row * cap + j;
+            if (j + 3u < (uint32_t)n) {
+                float4 p = *reinterpret_cast<float4*>(P + k);
+                const float4 g = *reinterpret_cast<const float4*>(G + k);
+                float4 m = *reinterpret_cast<float4*>(M + k);
+                float4 v = *reinterpret_cast<float4*>(V + k);
+                upd(p.x, g.x, m.x, v.x, lr);
+                upd(p.y, g.y, m.y, v.y, lr);
+                upd(p.z, g.z, m.z, v.z, lr);
+                upd(p.w, g.w, m.w, v.w, lr);
+                *reinterpret_cast<float4*>(P + k) = p;
+                *reinterpret_cast<float4*>(M + k) = m;
+                *reinterpret_cast<float4*>(V + k) = v;
+            } else {
+                for (uint32_t e = 0; e < 4u && j + e < (uint32_t)n; ++e)
+                    upd(P[k + e], G[k + e], M[k + e], V[k + e], lr);
+            }
         }
     }
     if (threadIdx.x == 0) {
-        const uint32_t total = gridDim.x * gridDim.y;
-        if (atomicAdd(st + 2, 1u) == total - 1u) {
+        if (atomicAdd(st + 2, 1u) == gridDim.x - 1u) {
             if (sbc[2] == 0.f) {
                 pw[0] = spw[0];
                 pw[1] = spw[1];
@@ -198,7 +204,8 @@ cudaError_t launch_adam(gs_ctx* c, cudaStream_t s) {
     a.b2 = c->cfg.beta2;
     a.eps = c->cfg.eps;
     ++c->launches;
-    dim3 grid(((c->n + 3) / 4 + 255) / 256, kParamRows);
+    const size_t groups = (size_t)kParamRows * ((c->n + 3) / 4);
+    const int grid = (int)std::min<size_t>((groups + 255) / 256, (size_t)c->num_sms * 8);
     k_adam<<<grid, 256, 0, s>>>(c->params, c->grads, c->adam_m, c->adam_v, c->n, c->cap, a, c->dcount, c->adam_pw);
     return cudaGetLastError();
 }
