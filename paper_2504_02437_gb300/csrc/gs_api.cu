@@ -339,7 +339,7 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         const size_t maxpix = (size_t)cfg->max_width * cfg->max_height;
         c->max_bins = (int)(V * ((cfg->max_width + 7) / 8) * ((cfg->max_height + 7) / 8));
         int64_t pc = cfg->pair_capacity > 0 ? cfg->pair_capacity : (int64_t)8 * cap * V;
-        pc = std::min<int64_t>(pc, 0xFFFFFFF0ll);
+        pc = std::min<int64_t>(pc, kMaxPairs);
         bool ok = true;
         ok = ok && dalloc(&c->params, kParamRows * cap) == cudaSuccess;
         ok = ok && dalloc(&c->grads, kParamRows * cap) == cudaSuccess;
@@ -495,7 +495,7 @@ int gs_render(gs_ctx* c, const gs_camera* cams, int n_views, float* rgb, float* 
     c->pairs_hint = (uint32_t)std::min<int64_t>(P, 0xFFFFFFFFll);
     if (P > c->pair_cap) {
         drop_graph(c);
-        if (alloc_pairs(c, std::min<int64_t>(P + P / 2 + 1024, 0xFFFFFFF0ll)) != cudaSuccess) {
+        if (alloc_pairs(c, std::min<int64_t>(P + P / 2 + 1024, kMaxPairs)) != cudaSuccess) {
             c->n_views = 0;
             return fail(c, GS_ERR_OOM, "growing the pair buffers failed");
         }
@@ -641,7 +641,7 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
         const uint32_t P = c->hflags[0];
         if (c->hflags[1] != 0u) {
             drop_graph(c);
-            if (alloc_pairs(c, std::min<int64_t>((int64_t)P + P / 2 + 4096, 0xFFFFFFF0ll)) != cudaSuccess)
+            if (alloc_pairs(c, std::min<int64_t>((int64_t)P + P / 2 + 4096, kMaxPairs)) != cudaSuccess)
                 return fail(c, GS_ERR_OOM, "growing the pair buffers failed");
             return fail(c, GS_ERR_CAPACITY, "an earlier iteration overflowed the pair buffer and skipped its update; "
                                             "the buffer has grown");
@@ -699,7 +699,7 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
     if ((code = gs_backward(c, nullptr, stream)) != GS_OK) return code;
     if ((code = gs_step(c, s)) != GS_OK) return code;
     const int64_t P = c->pairs_hint;
-    const int64_t want = std::min<int64_t>(P + P / 4 + 4096, 0xFFFFFFF0ll);
+    const int64_t want = std::min<int64_t>(P + P / 4 + 4096, kMaxPairs);
     if (want > c->pair_cap) {
         CK(cudaStreamSynchronize(s));
         if (alloc_pairs(c, want) != cudaSuccess) return fail(c, GS_ERR_OOM, "growing the pair buffers failed");

@@ -19,6 +19,9 @@ constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
 // Camera as the kernels read it (one per view, in device memory).
+// largest pair buffer (pair indices are 32-bit)
+constexpr int64_t kMaxPairs = 0xFFFFFFF0ll;
+
 struct DevCamera {
     float R[9];
     float t[3];
@@ -107,7 +110,9 @@ struct gs_ctx {
     // scratch
     uint32_t* hist = nullptr;               // radix / scan block counters
     int sort_blocks = 0;
-    uint32_t* dcount = nullptr;             // device scalars: [0] pairs, [1] overflow
+    uint32_t* dcount = nullptr;             // device scalars [8]: [0] pairs, [1] overflow, [2] Adam
+                                            // ticket, [3] UINT32_MAX, [4] Adam steps, [5] totals,
+                                            // [6], [7] work queues
     uint32_t* hcount = nullptr;             // pinned host mirror
     float* partials = nullptr;              // reduction partials
     float* fpart = nullptr;                 // photometric partials of the fused kernel (one per CTA)
@@ -188,6 +193,47 @@ cudaError_t launch_loss_tail(gs_ctx* c, const DevConst& k, const float* photo_pa
 cudaError_t launch_loss(gs_ctx* c, const DevConst& k, const float* rgb, const float* target, float* loss_out,
                         cudaStream_t s);
 cudaError_t launch_adam(gs_ctx* c, cudaStream_t s);
+
+// Adam (bias-corrected) with one learning rate per parameter row.
+struct AdamArgs {
+    float lr[kParamRows];
+    float b1, b2, eps;
+};
+AdamArgs adam_args(const gs_ctx* c);
+
+__device__ __forceinline__ void adam_update(float& p, float g, float& m, float& v, float lr, const AdamArgs& a,
+                                            float bc1, float bc2) {
+    m = a.b1 * m + (1.f - a.b1) * g;
+    v = a.b2 * v + (1.f - a.b2) * g * g;
+    const float mh = m / bc1, vh = v / bc2;
+    p -= lr * mh / (sqrtf(vh) + a.eps);
+}
+
+// Bias corrections of the next Adam step from device state (so that a graph
+// replays correctly): pw = {beta1^t, beta2^t} (float64 running products) after
+// t = st[4] completed steps; st[1] = pair-buffer overflow flag (step skipped).
+// Thread 0 of every CTA reads them before taking a ticket (st[2]); the last
+// CTA of the launch advances pw and t, so every CTA uses the same t + 1.
+__device__ __forceinline__ void adam_bias_begin(const AdamArgs& a, const uint32_t* st, const double* pw,
+                                                float* sbc, double* spw) {
+    const double p1 = pw[0] * (double)a.b1, p2 = pw[1] * (double)a.b2;
+    spw[0] = p1;
+    spw[1] = p2;
+    sbc[0] = (float)(1.0 - p1);
+    sbc[1] = (float)(1.0 - p2);
+    sbc[2] = st[1] != 0u ? 1.f : 0.f;
+}
+__device__ __forceinline__ void adam_bias_end(uint32_t* st, double* pw, const float* sbc, const double* spw,
+                                              uint32_t n_ctas) {
+    if (atomicAdd(st + 2, 1u) == n_ctas - 1u) {
+        if (sbc[2] == 0.f) {
+            pw[0] = spw[0];
+            pw[1] = spw[1];
+            st[4] += 1u;
+        }
+        st[2] = 0u;
+    }
+}
 cudaError_t launch_copy_T(gs_ctx* c, float* T_out, cudaStream_t s);
 // learned initialiser (k_mlp.cu): overwrite the staged plain parameters of the points
 cudaError_t mlp_initialise(gs_mlp* M, const DevCamera& cam, const float* image, const float* pts, int n, float* stage,

@@ -98,40 +98,19 @@ __global__ void __launch_bounds__(32) k_loss_final2(const float* __restrict__ ph
     }
 }
 
-struct AdamArgs {
-    float lr[kParamRows];
-    float b1, b2, eps;
-};
-
 // One Adam step over a persistent grid; each thread updates groups of 4
-// consecutive parameters of one row. The bias corrections come from device state, so that a captured graph
-// replays correctly: pw = {beta1^t, beta2^t} (float64 running products, no
-// pow) after t completed steps, st[4] = t, st[1] = pair-buffer overflow flag
-// of this iteration (the step is skipped), st[2] = ticket of the CTAs done.
-// Every CTA reads pw before it takes its ticket, and the last CTA advances
-// pw and t, so all CTAs of one launch use the same t + 1.
+// consecutive parameters of one row, with the bias corrections of
+// adam_bias_begin / adam_bias_end.
 __global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, const float* __restrict__ G,
                                               float* __restrict__ M, float* __restrict__ V, int n, int cap,
                                               AdamArgs a, uint32_t* __restrict__ st, double* __restrict__ pw) {
     __shared__ float sbc[3];
     __shared__ double spw[2];
-    if (threadIdx.x == 0) {
-        const double p1 = pw[0] * (double)a.b1, p2 = pw[1] * (double)a.b2;
-        spw[0] = p1;
-        spw[1] = p2;
-        sbc[0] = (float)(1.0 - p1);
-        sbc[1] = (float)(1.0 - p2);
-        sbc[2] = st[1] != 0u ? 1.f : 0.f;
-    }
+    if (threadIdx.x == 0) adam_bias_begin(a, st, pw, sbc, spw);
     __syncthreads();
     if (sbc[2] == 0.f) {
         const float bc1 = sbc[0], bc2 = sbc[1];
-        auto upd = [&](float& p, float g, float& m, float& v, float lr) {
-            m = a.b1 * m + (1.f - a.b1) * g;
-            v = a.b2 * v + (1.f - a.b2) * g * g;
-            const float mh = m / bc1, vh = v / bc2;
-            p -= lr * mh / (sqrtf(vh) + a.eps);
-        };
+        auto upd = [&](float& p, float g, float& m, float& v, float lr) { adam_update(p, g, m, v, lr, a, bc1, bc2); };
         // grid-stride over the 14 rows x ceil(n / 4) groups of 4 parameters
         const uint32_t nvec = (uint32_t)(n + 3) / 4u, total = nvec * (uint32_t)kParamRows;
         for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
@@ -156,16 +135,7 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, const float
             }
         }
     }
-    if (threadIdx.x == 0) {
-        if (atomicAdd(st + 2, 1u) == gridDim.x - 1u) {
-            if (sbc[2] == 0.f) {
-                pw[0] = spw[0];
-                pw[1] = spw[1];
-                st[4] += 1u;
-            }
-            st[2] = 0u;
-        }
-    }
+    if (threadIdx.x == 0) adam_bias_end(st, pw, sbc, spw, gridDim.x);
 }
 
 }  // namespace
@@ -195,14 +165,19 @@ cudaError_t launch_loss_tail(gs_ctx* c, const DevConst& k, const float* photo_pa
     return cudaGetLastError();
 }
 
-cudaError_t launch_adam(gs_ctx* c, cudaStream_t s) {
-    if (c->n == 0) return cudaSuccess;
+AdamArgs adam_args(const gs_ctx* c) {
     AdamArgs a;
     static const int group[kParamRows] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 2, 3, 4, 4, 4};
     for (int r = 0; r < kParamRows; ++r) a.lr[r] = c->cfg.lr[group[r]];
     a.b1 = c->cfg.beta1;
     a.b2 = c->cfg.beta2;
     a.eps = c->cfg.eps;
+    return a;
+}
+
+cudaError_t launch_adam(gs_ctx* c, cudaStream_t s) {
+    if (c->n == 0) return cudaSuccess;
+    const AdamArgs a = adam_args(c);
     ++c->launches;
     const size_t groups = (size_t)kParamRows * ((c->n + 3) / 4);
     const int grid = (int)std::min<size_t>((groups + 255) / 256, (size_t)c->num_sms * 8);
