@@ -77,6 +77,8 @@ typedef struct gs_config {
     float lambda_color;  /* Eq. 11 weight of the photometric term (1)                 */
     float lambda_reg;    /* Eq. 11 weight of the planar term (1)                      */
     float reg_floor;     /* Eq. 10 floor of min(s) (0.01)                             */
+    float lambda_photo;  /* Eq. 10 weight of L_SSIM = 1 - SSIM in L_color (0 = pure L1,
+                            the paper's value is 0.2); in [0, 1]                      */
     float beta1, beta2, eps;     /* Adam (0.9, 0.999, 1e-15)                          */
     float lr[5];         /* Adam learning rates: means, log-scales, quaternions,
                             opacity logits, colours (1e-3, 5e-3, 1e-3, 5e-2, 2.5e-3) */

@@ -34,7 +34,7 @@ class gs_config(C.Structure):
     _fields_ = [("near_z", C.c_float), ("fov_clamp", C.c_float), ("dilation", C.c_float),
                 ("lambda_floor", C.c_float), ("radius_sigma", C.c_float), ("alpha_min", C.c_float),
                 ("alpha_max", C.c_float), ("T_min", C.c_float), ("lambda_color", C.c_float),
-                ("lambda_reg", C.c_float), ("reg_floor", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("lambda_reg", C.c_float), ("reg_floor", C.c_float), ("lambda_photo", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
                 ("eps", C.c_float), ("lr", C.c_float * 5), ("split_thresh", C.c_float),
                 ("split_factor", C.c_float), ("insert_opacity", C.c_float), ("insert_tau", C.c_float),
                 ("clarity_sigma", C.c_float), ("tile_size", C.c_int32), ("pixels_per_thread", C.c_int32),

@@ -294,6 +294,7 @@ void gs_default_config(gs_config* f) {
     f->lambda_color = 1.f;
     f->lambda_reg = 1.f;
     f->reg_floor = 0.01f;
+    f->lambda_photo = 0.f;
     f->beta1 = 0.9f;
     f->beta2 = 0.999f;
     f->eps = 1e-15f;
@@ -323,6 +324,7 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
          cfg->pixels_per_thread != 4))
         return GS_ERR_ARG;
     if ((int64_t)cfg->capacity * cfg->max_views >= (int64_t)0xFFFFFFFF) return GS_ERR_ARG;
+    if (!(cfg->lambda_photo >= 0.f && cfg->lambda_photo <= 1.f)) return GS_ERR_ARG;
     gs_ctx* c = new gs_ctx();
     c->cfg = *cfg;
     c->device = device;
@@ -365,6 +367,11 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         ok = ok && dalloc(&c->grad2d, kGrad2dStride * V * cap) == cudaSuccess;
         ok = ok && dalloc(&c->hist, (size_t)256 * c->sort_blocks + 256) == cudaSuccess;
         ok = ok && dalloc(&c->dcount, 8) == cudaSuccess;
+        if (cfg->lambda_photo > 0.f) {
+            ok = ok && dalloc(&c->ssim_maps, (size_t)3 * 3 * V * maxpix) == cudaSuccess;
+            ok = ok && dalloc(&c->ssim_part, (size_t)2 * ssim_blocks(cfg->max_width, cfg->max_height,
+                                                                       cfg->max_views)) == cudaSuccess;
+        }
         ok = ok && dalloc(&c->partials, (size_t)c->n_partials + 8) == cudaSuccess;
         c->n_fpart = 32 * c->num_sms;   // at most 32 resident CTAs per SM
         ok = ok && dalloc(&c->fpart, (size_t)c->n_fpart) == cudaSuccess;
@@ -407,7 +414,8 @@ void gs_destroy(gs_ctx* c) {
     for (auto e : c->tpool) cudaEventDestroy(e);
     void* ptrs[] = {c->params, c->grads, c->adam_m, c->adam_v, c->dens_sum, c->dens_cnt, c->dom_cnt, c->adam_pw, c->dcam, c->rec,
                     c->tiles_touched, c->depth, c->dkey[0], c->dkey[1], c->dval[0], c->dval[1], c->offsets, c->ranges,
-                    c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->dcount, c->partials, c->fpart,
+                    c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->ssim_maps, c->ssim_part, c->dcount,
+                    c->partials, c->fpart,
                     c->own_rgb};
     for (void* p : ptrs) cudaFree(p);
     free_pairs(c);
@@ -517,7 +525,12 @@ int gs_loss(gs_ctx* c, const float* target, float* loss_dev, void* stream) {
     float* out = loss_dev ? loss_dev : c->partials + c->n_partials;
     const DevConst k = dev_const(c->cfg);
     Phase ph(c, GS_PHASE_LOSS, s);
-    CK(launch_loss(c, k, c->rendered_rgb, target, out, s));
+    if (c->cfg.lambda_photo > 0.f) {
+        CK(launch_ssim_loss(c, k, c->rendered_rgb, target, c->ssim_part, s));
+        CK(launch_loss_tail(c, k, c->ssim_part, 2 * ssim_blocks(c->width, c->height, c->n_views), out, s));
+    } else {
+        CK(launch_loss(c, k, c->rendered_rgb, target, out, s));
+    }
     c->loss_ready = true;
     return GS_OK;
 }
@@ -720,19 +733,34 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
         ++c->launches;
         k_set_cams<<<1, 32, 0, cs>>>(b, dst);
         cc = front_half(c, k, cs);
-        if (cc == GS_OK) cc = back_half(c, k, nullptr, nullptr, cs);
+        const bool ssim = c->cfg.lambda_photo > 0.f;
+        // with the SSIM term dL/dC needs the whole image: forward, loss, adjoint as three kernels;
+        // with pure L1 one fused kernel per (view, tile)
+        if (cc == GS_OK) cc = back_half(c, k, ssim ? rgb : nullptr, nullptr, cs);
+        if (cc == GS_OK && ssim) {
+            Phase ph(c, GS_PHASE_LOSS, cs);
+            if (launch_ssim_loss(c, k, rgb, target, c->ssim_part, cs) != cudaSuccess ||
+                launch_loss_tail(c, k, c->ssim_part, 2 * ssim_blocks(c->width, c->height, c->n_views), loss_out,
+                                 cs) != cudaSuccess)
+                cc = GS_ERR_CUDA;
+        }
         if (cc == GS_OK &&
             cudaMemsetAsync(c->grad2d, 0, sizeof(float) * kGrad2dStride * c->n_views * (size_t)c->n, cs) != cudaSuccess)
             cc = GS_ERR_CUDA;
-        int fgrid = 0;
-        if (cc == GS_OK) {
-            Phase ph(c, GS_PHASE_RASTER_FUSED, cs);
-            if (launch_raster_fused(c, k, target, rgb, c->fpart, c->n_fpart, &fgrid, cs) != cudaSuccess)
-                cc = GS_ERR_CUDA;
-        }
-        if (cc == GS_OK) {
-            Phase ph(c, GS_PHASE_LOSS, cs);
-            if (launch_loss_tail(c, k, c->fpart, fgrid, loss_out, cs) != cudaSuccess) cc = GS_ERR_CUDA;
+        if (cc == GS_OK && ssim) {
+            Phase ph(c, GS_PHASE_RASTER_BWD, cs);
+            if (launch_raster_backward(c, k, c->dLdC, cs) != cudaSuccess) cc = GS_ERR_CUDA;
+        } else if (cc == GS_OK) {
+            int fgrid = 0;
+            {
+                Phase ph(c, GS_PHASE_RASTER_FUSED, cs);
+                if (launch_raster_fused(c, k, target, rgb, c->fpart, c->n_fpart, &fgrid, cs) != cudaSuccess)
+                    cc = GS_ERR_CUDA;
+            }
+            if (cc == GS_OK) {
+                Phase ph(c, GS_PHASE_LOSS, cs);
+                if (launch_loss_tail(c, k, c->fpart, fgrid, loss_out, cs) != cudaSuccess) cc = GS_ERR_CUDA;
+            }
         }
         if (cc == GS_OK) {
             Phase ph(c, GS_PHASE_PROJECT_BWD, cs);

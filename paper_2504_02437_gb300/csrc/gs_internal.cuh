@@ -109,6 +109,8 @@ struct gs_ctx {
 
     // scratch
     uint32_t* hist = nullptr;               // radix / scan block counters
+    float* ssim_maps = nullptr;             // [3][V][3][H][W] SSIM derivative maps (lambda_photo > 0)
+    float* ssim_part = nullptr;             // [2 ssim_blocks] per-CTA photometric loss terms
     int sort_blocks = 0;
     uint32_t* dcount = nullptr;             // device scalars [8]: [0] pairs, [1] overflow, [2] Adam
                                             // ticket, [3] UINT32_MAX, [4] Adam steps, [5] totals,
@@ -193,6 +195,9 @@ cudaError_t launch_loss_tail(gs_ctx* c, const DevConst& k, const float* photo_pa
 cudaError_t launch_loss(gs_ctx* c, const DevConst& k, const float* rgb, const float* target, float* loss_out,
                         cudaStream_t s);
 cudaError_t launch_adam(gs_ctx* c, cudaStream_t s);
+int ssim_blocks(int width, int height, int n_views);
+cudaError_t launch_ssim_loss(gs_ctx* c, const DevConst& k, const float* rgb, const float* target, float* partials,
+                             cudaStream_t s);
 
 // Adam (bias-corrected) with one learning rate per parameter row.
 struct AdamArgs {

@@ -65,6 +65,7 @@ def test_default_config_is_the_documented_reading(lib):
     cfg = N.gs_config()
     lib.gs_default_config(C.byref(cfg))
     assert cfg.reg_floor == pytest.approx(0.01)            # Eq. 10
+    assert cfg.lambda_photo == 0.0                          # pure L1 unless the SSIM term is asked for
     assert cfg.alpha_min == pytest.approx(1 / 255)
     assert cfg.alpha_max == pytest.approx(0.99)
     assert cfg.T_min == pytest.approx(1e-4)
