@@ -571,6 +571,52 @@ def run_stream_bench(args):
     return 0
 
 
+ABLATION_METRIC = "synthetic ablation of the mapping stream: PSNR, #Gaussians, iters/s per switch setting"
+ABLATIONS = [
+    ("full: opacity insertion, gradient split, planar term", {}),
+    ("no planar term", {"lambda_reg": 0.0}),
+    ("no densification", {"densify": False}),
+    ("distance insertion (tau 0.05 m)", {"insert_tau": 0.05}),
+    ("gradient + clarity split (sigma 64 px)", {"clarity_sigma": 64.0, "clarity": True}),
+    ("L1 + SSIM (lambda_photo 0.2)", {"lambda_photo": 0.2}),
+]
+
+
+def run_ablation_bench(args):
+    """The switches of the paper's ablation (insertion rule, densification, planar term; Table 4's
+    analogue) and the SSIM term on one synthetic stream: per setting the newest keyframe's PSNR
+    after its iterations (mean of the last 20 keyframes), the final Gaussian count and the
+    mapping iterations/s."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2504_02437_gb300 import build as B
+    B.build()
+    from synth import stream_sequence
+    from paper_2504_02437_gb300 import stream as S
+    from paper_2504_02437_gb300.api import GaussianMap
+    cams, tg, pts = stream_sequence(0, args.frames)
+    rows = []
+    with ClockSampler(0) as clk:
+        for name, sw in ABLATIONS:
+            cfg = {k: v for k, v in sw.items() if k not in ("densify", "clarity")}
+            gm = GaussianMap(capacity=STREAM_CAPACITY, max_views=8, max_width=640, max_height=480,
+                             tile_size=args.tile, pixels_per_thread=args.ppt, **cfg)
+            st = S.run_stream(gm, cams, tg, pts, iters=100, track_psnr="final", densify=sw.get("densify", True),
+                              clarity=sw.get("clarity", False))
+            gm.close()
+            ps = st["psnr"].tolist()
+            rows.append({"setting": name, "psnr_mean_last_20": float(np.mean(ps[-20:])),
+                         "psnr_mean_all": float(np.mean(ps)), "n_gaussians_final": st["n_gauss"][-1],
+                         "iters_per_s": st["iters_per_s"]})
+    line = {"metric": ABLATION_METRIC, "value": rows[0]["psnr_mean_last_20"], "unit": "dB (full setting)",
+            "n_gpus": 1, "steps": args.frames * 100, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": STREAM_WORKLOAD.format(F=args.frames, I=100)},
+            "ablation": rows, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ttp_bench(args):
     import torch
     torch.cuda.set_device(0)
@@ -595,8 +641,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, default=0, choices=[0, 8, 16])
-    ap.add_argument("--workload", default="replica", choices=["replica", "window", "stream", "learned_init"])
-    ap.add_argument("--frames", type=int, default=200)
+    ap.add_argument("--workload", default="replica", choices=["replica", "window", "stream", "learned_init",
+                                                              "ablation"])
+    ap.add_argument("--frames", type=int, default=0, help="keyframes (stream, learned_init: 200; ablation: 60)")
     ap.add_argument("--train-seeds", type=int, default=5)
     ap.add_argument("--heldout-seeds", type=int, default=5)
     ap.add_argument("--ppt", type=int, default=0, choices=[0, 1, 2, 4])
@@ -609,10 +656,15 @@ def main():
         return run_reference(args)
     if args.workload == "window":
         return run_window(args)
+    if args.workload in ("stream", "learned_init"):
+        args.frames = args.frames or 200
     if args.workload == "stream":
         return run_stream_bench(args)
     if args.workload == "learned_init":
         return run_ttp_bench(args)
+    if args.workload == "ablation":
+        args.frames = args.frames or 60
+        return run_ablation_bench(args)
     return run_ours(args)
 
 

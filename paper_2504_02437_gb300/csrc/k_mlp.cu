@@ -5,9 +5,10 @@
 // a Gaussian inserted at a VO point from the keyframe's 5x5 patch around the
 // point, its depth and its camera-frame position.
 //
-// Every matrix product is one strided GEMM C (+)= A B on mma.sync m16n8k16
-// (bf16 operands, f32 accumulators): forward X W^T, input gradients dZ W and
-// weight gradients dZ^T X (split over the batch with f32 atomics). Upstream
+// Every matrix product is one strided GEMM C (+)= A B on tcgen05.mma (bf16
+// operands in shared memory, f32 accumulators in TMEM): forward X W^T, input
+// gradients dZ W and weight gradients dZ^T X (split over the batch with f32
+// atomics). Upstream
 // gradients dZ enter as bf16 hi + lo pairs (two products), so the backward
 // keeps ~16 mantissa bits where one bf16 rounding would keep 8.
 #include <cuda_bf16.h>
@@ -27,86 +28,193 @@ constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid, 
 
 typedef __nv_bfloat16 bf16;
 
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+// ---- the strided GEMM C (+)= A B, A(m, k) = A[m sam + k sak], B(k, n) = B[k sbk + n sbn] (bf16),
+// on the 5th-generation tensor cores (tcgen05, TMEM accumulators) ----
+//
+// One CTA of 4 warps computes a 128 x NT tile of C. Its K range is walked in
+// chunks of 64: all threads gather the A (128 x 64) and B (NT x 64) chunks
+// from their strided global layout into shared memory in the canonical
+// K-major, non-swizzled UMMA layout (8 x 16-byte core matrices; the core at
+// row group g and K group j sits at g * 1024 + j * 128 bytes, so the leading
+// (K) byte offset is 128 and the stride (row-group) byte offset 1024), then one
+// elected thread issues four tcgen05.mma (M = 128, N = NT, K = 16, BF16 in,
+// FP32 accumulate in TMEM) and commits them to an mbarrier that all threads
+// wait on before the chunk is restaged. The epilogue reads the accumulator
+// with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. tile rows) and
+// stores, accumulates or atomically adds it into C. Every wait is bounded: a
+// wait that gives up sets *err, and the CTA still frees its TMEM.
+constexpr int kTcM = 128, kTcKC = 64;
+constexpr uint32_t kTcWaitLimit = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+// tcgen05 shared-memory matrix descriptor: start address, leading and stride
+// byte offsets (all >> 4), the fixed version bits 46..48 = 0b001, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor of kind::f16: D = F32 (bits 4..5), A = B = BF16 (bits 7..9,
+// 10..12), both K-major (bits 15, 16 clear), N >> 3 in bits 17..22, M >> 4 in 24..28
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kTcWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
 }
 
-// C[M][N] (ldc) = A B (mode 0), += A B with f32 atomics (mode 1, split-K) or
-// += A B (mode 2), A(m, k) = A[m sam + k sak], B(k, n) = B[k sbk + n sbn] (bf16),
-// over k in this CTA's split of [0, K). 64 x 64 tile per CTA, 4 warps of 32 x 32
-// (2 x 4 mma tiles). Out-of-range elements are staged as zeros.
-constexpr int kGT = 64, kGK = 16, kGPad = 8;
-
-__global__ void __launch_bounds__(128) k_gemm_bf16(const bf16* __restrict__ A, long sam, long sak,
-                                                   const bf16* __restrict__ B, long sbk, long sbn,
-                                                   float* __restrict__ C, int ldc, int M, int N, int K, int k_split,
-                                                   int atomic) {
-    __shared__ __align__(16) bf16 As[kGT][kGK + kGPad];   // [m][k]
-    __shared__ __align__(16) bf16 Bs[kGT][kGK + kGPad];   // [n][k]
-    const int m0 = blockIdx.y * kGT, n0 = blockIdx.x * kGT;
-    const int kb = blockIdx.z * k_split, ke = min(K, kb + k_split);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int g = lane >> 2, t = lane & 3;
-    float acc[2][4][4];
+// Gather one 64-wide K chunk of a (rows x K) operand X(r, k) = X[r * s_r + k * s_k] into the
+// canonical layout; zero outside rows < R_valid and k < k_end.
+__device__ __forceinline__ void tc_stage(uint8_t* dst, int rows, const bf16* __restrict__ X, long s_r, long s_k,
+                                         int r0, int R_valid, int k0, int k_end) {
+    const bool kvec = s_k == 1 && (s_r % 8) == 0 && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    if (kvec) {
+        // one 16-byte core-matrix row (8 consecutive k) per step
+        for (int e = threadIdx.x; e < rows * (kTcKC / 8); e += 128) {
+            const int r = e / (kTcKC / 8), j = e - r * (kTcKC / 8);
+            const int gr = r0 + r, gk = k0 + 8 * j;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (gr < R_valid) {
+                if (gk + 8 <= k_end) {
+                    v = *reinterpret_cast<const uint4*>(X + (long)gr * s_r + gk);
+                } else {
+                    bf16 t[8];
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-    const bf16 zero = __float2bfloat16_rn(0.f);
-    for (int k0 = kb; k0 < ke; k0 += kGK) {
-        for (int e = threadIdx.x; e < kGT * kGK; e += 128) {
-            const int r = e / kGK, kk = e % kGK;
-            const int m = m0 + r, n = n0 + r, k = k0 + kk;
-            As[r][kk] = (m < M && k < ke) ? A[(long)m * sam + (long)k * sak] : zero;
-            Bs[r][kk] = (n < N && k < ke) ? B[(long)k * sbk + (long)n * sbn] : zero;
-        }
-        __syncthreads();
-        uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int r = wm + 16 * i + g;
-            af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][2 * t]);
-            af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][2 * t]);
-            af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][2 * t + 8]);
-            af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][2 * t + 8]);
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int c = wn + 8 * j + g;
-            bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][2 * t]);
-            bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][2 * t + 8]);
-        }
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) mma_bf16_16816(acc[i][j], af[i], bfr[j]);
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int m = m0 + wm + 16 * i + g + (e >= 2 ? 8 : 0);
-                const int n = n0 + wn + 8 * j + 2 * t + (e & 1);
-                if (m < M && n < N) {
-                    float* dst = C + (long)m * ldc + n;
-                    if (atomic == 1)
-                        atomicAdd(dst, acc[i][j][e]);
-                    else if (atomic == 2)
-                        *dst += acc[i][j][e];
-                    else
-                        *dst = acc[i][j][e];
+                    for (int q = 0; q < 8; ++q)
+                        t[q] = gk + q < k_end ? X[(long)gr * s_r + gk + q] : __float2bfloat16_rn(0.f);
+                    v = *reinterpret_cast<const uint4*>(t);
                 }
             }
+            *reinterpret_cast<uint4*>(dst + (r >> 3) * 1024 + j * 128 + (r & 7) * 16) = v;
+        }
+    } else {
+        // element by element, consecutive threads along the unit-stride dimension
+        const bool r_fast = s_r == 1;
+        for (int e = threadIdx.x; e < rows * kTcKC; e += 128) {
+            int r, k;
+            if (r_fast) {
+                k = e / rows;
+                r = e - k * rows;
+            } else {
+                r = e / kTcKC;
+                k = e - r * kTcKC;
+            }
+            const int gr = r0 + r, gk = k0 + k;
+            const bf16 v = (gr < R_valid && gk < k_end) ? X[(long)gr * s_r + (long)gk * s_k] : __float2bfloat16_rn(0.f);
+            *reinterpret_cast<bf16*>(dst + (r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2) = v;
+        }
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(128) k_gemm_tc(const bf16* __restrict__ A, long sam, long sak,
+                                                 const bf16* __restrict__ B, long sbk, long sbn,
+                                                 float* __restrict__ C, int ldc, int M, int N, int K, int k_split,
+                                                 int mode, uint32_t* __restrict__ err) {
+    static_assert(NT % 16 == 0 && NT >= 16 && NT <= 128, "UMMA N for M = 128");
+    constexpr uint32_t kCols = NT <= 32 ? 32u : (NT <= 64 ? 64u : 128u);
+    __shared__ __align__(1024) uint8_t sa[kTcM * kTcKC * 2];
+    __shared__ __align__(1024) uint8_t sb[NT * kTcKC * 2];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * NT;
+    const int kb = blockIdx.z * k_split, ke = min(K, kb + k_split);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t bar = smem_u32(&mbar);
+    const uint32_t a_base = smem_u32(sa), b_base = smem_u32(sb);
+    constexpr uint32_t idesc = umma_idesc_bf16(kTcM, NT);
+    bool ok = true, issued = false;
+    uint32_t parity = 0;
+    for (int k0 = kb; k0 < ke && ok; k0 += kTcKC) {
+        tc_stage(sa, kTcM, A, sam, sak, m0, M, k0, ke);
+        tc_stage(sb, NT, B, sbn, sbk, n0, N, k0, ke);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int kk = 0; kk < kTcKC / 16; ++kk) {
+                const uint64_t ad = umma_desc(a_base + kk * 256, 128, 1024);
+                const uint64_t bd = umma_desc(b_base + kk * 256, 128, 1024);
+                const uint32_t acc = (issued || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                         : "memory");
+        }
+        issued = true;
+        ok = mbar_wait(bar, parity);
+        parity ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (ok) {
+        const int m = m0 + warp * 32 + lane;
+#pragma unroll
+        for (int c0 = 0; c0 < NT; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(taddr)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (m < M) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + c0 + j;
+                    if (n >= N) continue;
+                    const float val = issued ? __uint_as_float(v[j]) : 0.f;
+                    float* dst = C + (long)m * ldc + n;
+                    if (mode == 1) {
+                        if (issued) atomicAdd(dst, val);
+                    } else if (mode == 2) {
+                        *dst += val;
+                    } else {
+                        *dst = val;
+                    }
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicOr(err, 1u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+    }
 }
 
 __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
@@ -295,6 +403,8 @@ struct gs_mlp {
     bf16* dz = nullptr;      // [rows][128] pre-activation gradient, bf16 hi part
     bf16* dz_lo = nullptr;   // ... and lo part
     float* part = nullptr;   // loss partials
+    uint32_t* err = nullptr;   // device flag: a tensor-core wait gave up
+    uint32_t* herr = nullptr;  // pinned copy of it, refreshed after each forward / backward
 };
 
 namespace {
@@ -333,16 +443,26 @@ int mlp_rows(gs_mlp* M, int rows) {
     return GS_OK;
 }
 
+// C (+)= A B on the tcgen05 tensor cores; split-K (f32 atomics) when `split`.
 void gemm(const bf16* A, long sam, long sak, const bf16* B, long sbk, long sbn, float* C, int ldc, int M, int N,
-          int K, bool split, cudaStream_t s, bool accumulate = false) {
+          int K, bool split, cudaStream_t s, uint32_t* err, bool accumulate = false) {
     int splits = 1, kps = K;
     if (split) {
         splits = std::max(1, std::min(256, K / 1024));
-        kps = ((K + splits - 1) / splits + kGK - 1) / kGK * kGK;
+        kps = ((K + splits - 1) / splits + kTcKC - 1) / kTcKC * kTcKC;
         splits = (K + kps - 1) / kps;
     }
-    dim3 grid((N + kGT - 1) / kGT, (M + kGT - 1) / kGT, splits);
-    k_gemm_bf16<<<grid, 128, 0, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, kps, split ? 1 : (accumulate ? 2 : 0));
+    const int mode = split ? 1 : (accumulate ? 2 : 0);
+    const int nt = N <= 16 ? 16 : (N <= 32 ? 32 : (N <= 64 ? 64 : 128));
+    dim3 grid((N + nt - 1) / nt, (M + kTcM - 1) / kTcM, splits);
+    if (nt == 16)
+        k_gemm_tc<16><<<grid, 128, 0, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, kps, mode, err);
+    else if (nt == 32)
+        k_gemm_tc<32><<<grid, 128, 0, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, kps, mode, err);
+    else if (nt == 64)
+        k_gemm_tc<64><<<grid, 128, 0, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, kps, mode, err);
+    else
+        k_gemm_tc<128><<<grid, 128, 0, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, kps, mode, err);
 }
 
 // forward of `rows` feature rows (f32 [rows][80]) into M->y [rows][16]
@@ -351,11 +471,11 @@ cudaError_t mlp_forward_rows(gs_mlp* M, const float* feat, int rows, cudaStream_
     const bf16* W2 = W1 + kHid * kIn;
     const bf16* W3 = W2 + kHid * kHid;
     k_to_bf16<<<kEwBlocks, kEwThreads, 0, s>>>(feat, M->xb, (long)rows * kIn);
-    gemm(M->xb, kIn, 1, W1, 1, kIn, M->z1, kHid, rows, kHid, kIn, false, s);
+    gemm(M->xb, kIn, 1, W1, 1, kIn, M->z1, kHid, rows, kHid, kIn, false, s, M->err);
     k_bias_gelu<<<kEwBlocks, kEwThreads, 0, s>>>(M->z1, M->p + kOffB1, M->h1, (long)rows * kHid, kHid);
-    gemm(M->h1, kHid, 1, W2, 1, kHid, M->z2, kHid, rows, kHid, kHid, false, s);
+    gemm(M->h1, kHid, 1, W2, 1, kHid, M->z2, kHid, rows, kHid, kHid, false, s, M->err);
     k_bias_gelu<<<kEwBlocks, kEwThreads, 0, s>>>(M->z2, M->p + kOffB2, M->h2, (long)rows * kHid, kHid);
-    gemm(M->h2, kHid, 1, W3, 1, kHid, M->y, kOutPad, rows, kOutPad, kHid, false, s);
+    gemm(M->h2, kHid, 1, W3, 1, kHid, M->y, kOutPad, rows, kOutPad, kHid, false, s, M->err);
     k_bias<<<kEwBlocks, kEwThreads, 0, s>>>(M->y, M->p + kOffB3, (long)rows * kOutPad, kOutPad);
     return cudaGetLastError();
 }
@@ -378,6 +498,9 @@ int gs_mlp_create(int device, uint64_t seed, gs_mlp** out) {
     ok = ok && cudaMalloc(&M->v, sizeof(float) * kParams) == cudaSuccess;
     ok = ok && cudaMalloc(&M->wb, sizeof(bf16) * (kHid * kIn + kHid * kHid + kOutPad * kHid)) == cudaSuccess;
     ok = ok && cudaMalloc(&M->part, sizeof(float) * (kEwBlocks + 1)) == cudaSuccess;
+    ok = ok && cudaMalloc(&M->err, sizeof(uint32_t)) == cudaSuccess && cudaMemset(M->err, 0, sizeof(uint32_t)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void**)&M->herr, sizeof(uint32_t)) == cudaSuccess;
+    if (ok) *M->herr = 0u;
     if (!ok) {
         gs_mlp_destroy(M);
         return GS_ERR_OOM;
@@ -412,8 +535,9 @@ void gs_mlp_destroy(gs_mlp* M) {
     if (!M) return;
     cudaSetDevice(M->device);
     mlp_free_rows(M);
-    void* ps[] = {M->p, M->g, M->m, M->v, M->wb, M->part};
+    void* ps[] = {M->p, M->g, M->m, M->v, M->wb, M->part, M->err};
     for (void* q : ps) cudaFree(q);
+    if (M->herr) cudaFreeHost(M->herr);
     delete M;
 }
 
@@ -470,10 +594,13 @@ int gs_mlp_forward(gs_mlp* M, const float* feat_dev, int n, float* out_dev, void
     if (!M || n < 0 || (n > 0 && (!feat_dev || !out_dev))) return GS_ERR_ARG;
     if (n == 0) return GS_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    if (*M->herr != 0u) return GS_ERR_CUDA;   // a tensor-core wait of an earlier call gave up
     if (mlp_rows(M, n) != GS_OK) return GS_ERR_OOM;
     if (mlp_forward_rows(M, feat_dev, n, s) != cudaSuccess) return GS_ERR_CUDA;
-    return cudaMemcpyAsync(out_dev, M->y, sizeof(float) * (size_t)n * kOutPad, cudaMemcpyDeviceToDevice, s) ==
-                   cudaSuccess
+    if (cudaMemcpyAsync(out_dev, M->y, sizeof(float) * (size_t)n * kOutPad, cudaMemcpyDeviceToDevice, s) !=
+        cudaSuccess)
+        return GS_ERR_CUDA;
+    return cudaMemcpyAsync(M->herr, M->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) == cudaSuccess
                ? GS_OK
                : GS_ERR_CUDA;
 }
@@ -481,6 +608,7 @@ int gs_mlp_forward(gs_mlp* M, const float* feat_dev, int n, float* out_dev, void
 int gs_mlp_backward(gs_mlp* M, const float* feat_dev, const float* target_dev, int n, float* loss_dev, void* stream) {
     if (!M || n <= 0 || !feat_dev || !target_dev) return GS_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    if (*M->herr != 0u) return GS_ERR_CUDA;   // a tensor-core wait of an earlier call gave up
     if (mlp_rows(M, n) != GS_OK) return GS_ERR_OOM;
     if (mlp_forward_rows(M, feat_dev, n, s) != cudaSuccess) return GS_ERR_CUDA;
     const bf16* W2 = M->wb + kHid * kIn;
@@ -490,20 +618,21 @@ int gs_mlp_backward(gs_mlp* M, const float* feat_dev, const float* target_dev, i
     if (loss_dev) k_sum_partials<<<1, 32, 0, s>>>(M->part, kEwBlocks, loss_dev);
     // Upstream gradients enter the tensor cores as bf16 hi + lo pairs: two products each.
     // output layer: dW3 = dY^T H2, dH2 = dY W3
-    for (const bf16* d : {M->dy, M->dy_lo}) gemm(d, 1, kOutPad, M->h2, kHid, 1, M->g + kOffW3, kHid, kOutPad, kHid, n, true, s);
-    gemm(M->dy, kOutPad, 1, W3, kHid, 1, M->dh, kHid, n, kHid, kOutPad, false, s);
-    gemm(M->dy_lo, kOutPad, 1, W3, kHid, 1, M->dh, kHid, n, kHid, kOutPad, false, s, true);
+    for (const bf16* d : {M->dy, M->dy_lo}) gemm(d, 1, kOutPad, M->h2, kHid, 1, M->g + kOffW3, kHid, kOutPad, kHid, n, true, s, M->err);
+    gemm(M->dy, kOutPad, 1, W3, kHid, 1, M->dh, kHid, n, kHid, kOutPad, false, s, M->err);
+    gemm(M->dy_lo, kOutPad, 1, W3, kHid, 1, M->dh, kHid, n, kHid, kOutPad, false, s, M->err, true);
     k_gelu_back<<<kEwBlocks, kEwThreads, 0, s>>>(M->dh, M->z2, M->dz, M->dz_lo, M->g + kOffB2, n);
     // second layer: dW2 = dZ2^T H1, dH1 = dZ2 W2
-    for (const bf16* d : {M->dz, M->dz_lo}) gemm(d, 1, kHid, M->h1, kHid, 1, M->g + kOffW2, kHid, kHid, kHid, n, true, s);
-    gemm(M->dz, kHid, 1, W2, kHid, 1, M->dh, kHid, n, kHid, kHid, false, s);
-    gemm(M->dz_lo, kHid, 1, W2, kHid, 1, M->dh, kHid, n, kHid, kHid, false, s, true);
+    for (const bf16* d : {M->dz, M->dz_lo}) gemm(d, 1, kHid, M->h1, kHid, 1, M->g + kOffW2, kHid, kHid, kHid, n, true, s, M->err);
+    gemm(M->dz, kHid, 1, W2, kHid, 1, M->dh, kHid, n, kHid, kHid, false, s, M->err);
+    gemm(M->dz_lo, kHid, 1, W2, kHid, 1, M->dh, kHid, n, kHid, kHid, false, s, M->err, true);
     k_gelu_back<<<kEwBlocks, kEwThreads, 0, s>>>(M->dh, M->z1, M->dz, M->dz_lo, M->g + kOffB1, n);
     // first layer: dW1 = dZ1^T X
-    for (const bf16* d : {M->dz, M->dz_lo}) gemm(d, 1, kHid, M->xb, kIn, 1, M->g + kOffW1, kIn, kHid, kIn, n, true, s);
+    for (const bf16* d : {M->dz, M->dz_lo}) gemm(d, 1, kHid, M->xb, kIn, 1, M->g + kOffW1, kIn, kHid, kIn, n, true, s, M->err);
     // the padding rows of the output layer are not trained
     cudaMemsetAsync(M->g + kOffW3 + kOut * kHid, 0, sizeof(float) * (kOutPad - kOut) * kHid, s);
     cudaMemsetAsync(M->g + kOffB3 + kOut, 0, sizeof(float) * (kOutPad - kOut), s);
+    cudaMemcpyAsync(M->herr, M->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
