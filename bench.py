@@ -571,6 +571,70 @@ def run_stream_bench(args):
     return 0
 
 
+MLP_METRIC = "learned-initialiser MLP training steps/s (forward + backward + Adam, 4096 rows, BF16 tcgen05)"
+# FLOP per row of one training step: forward 2 x (80x128 + 128x128 + 128x16); the backward repeats
+# every product that takes an upstream gradient twice (bf16 hi + lo): weight gradients of the three
+# layers and input gradients of the two hidden layers
+MLP_FLOP_FWD_PER_ROW = 2 * (80 * 128 + 128 * 128 + 128 * 16)
+MLP_FLOP_BWD_PER_ROW = 2 * 2 * (16 * 128 + 128 * 128 + 128 * 80) + 2 * 2 * (16 * 128 + 128 * 128)
+
+
+def run_mlp_bench(args):
+    """Training steps of the learned initialiser on random features (the shapes of config 5's
+    training batches): one step = forward, MSE backward, Adam. Tensor-core roofline against the
+    measured BF16 peak."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2504_02437_gb300 import build as B
+    B.build()
+    from paper_2504_02437_gb300.api import MLP
+    rows = 4096
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    X = torch.rand(rows, 80, device="cuda", generator=g)
+    Y = torch.randn(rows, 16, device="cuda", generator=g) * 0.5
+    Y[:, 11:] = 0
+    mlp = MLP(seed=0)
+    for _ in range(args.warmup):
+        mlp.backward(X, Y)
+        mlp.step(1e-3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        for a, b in ev:
+            a.record()
+            mlp.backward(X, Y)
+            mlp.step(1e-3)
+            b.record()
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    # forward alone on an insertion batch (96 points)
+    Xs = X[:96].contiguous()
+    evf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in evf:
+        a.record()
+        mlp.forward(Xs)
+        b.record()
+    torch.cuda.synchronize()
+    ms_fwd96 = sum(a.elapsed_time(b) for a, b in evf) / args.steps
+    flops = rows * (MLP_FLOP_FWD_PER_ROW + MLP_FLOP_BWD_PER_ROW)
+    peaks, src = _peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    ach = flops / (ms * 1e-3) / 1e12
+    line = {"metric": MLP_METRIC, "value": 1000.0 / ms, "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 (f32 accumulate)", "data": "synthetic",
+            "config": {"workload": "MLP 80-128-128-16 training step on 4096 random feature rows",
+                       "l2": "resident (the whole step fits in L2; the MLP is latency-bound)"},
+            "forward_96_rows_ms": ms_fwd96,
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "traffic": None, "kernel": "whole training step (13 k_gemm_tc launches + elementwise)",
+                         "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({src})"},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 ABLATION_METRIC = "synthetic ablation of the mapping stream: PSNR, #Gaussians, iters/s per switch setting"
 ABLATIONS = [
     ("full: opacity insertion, gradient split, planar term", {}),
@@ -642,7 +706,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", type=int, default=0, choices=[0, 8, 16])
     ap.add_argument("--workload", default="replica", choices=["replica", "window", "stream", "learned_init",
-                                                              "ablation"])
+                                                              "ablation", "mlp"])
     ap.add_argument("--frames", type=int, default=0, help="keyframes (stream, learned_init: 200; ablation: 60)")
     ap.add_argument("--train-seeds", type=int, default=5)
     ap.add_argument("--heldout-seeds", type=int, default=5)
@@ -662,6 +726,8 @@ def main():
         return run_stream_bench(args)
     if args.workload == "learned_init":
         return run_ttp_bench(args)
+    if args.workload == "mlp":
+        return run_mlp_bench(args)
     if args.workload == "ablation":
         args.frames = args.frames or 60
         return run_ablation_bench(args)

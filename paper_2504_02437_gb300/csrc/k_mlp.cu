@@ -446,14 +446,18 @@ int mlp_rows(gs_mlp* M, int rows) {
 // C (+)= A B on the tcgen05 tensor cores; split-K (f32 atomics) when `split`.
 void gemm(const bf16* A, long sam, long sak, const bf16* B, long sbk, long sbn, float* C, int ldc, int M, int N,
           int K, bool split, cudaStream_t s, uint32_t* err, bool accumulate = false) {
+    // these products are small (a few MFLOP): spread them over more CTAs, narrower N tiles
+    // for the row-parallel products and K splits of 256 rows for the weight gradients
     int splits = 1, kps = K;
     if (split) {
-        splits = std::max(1, std::min(256, K / 1024));
+        splits = std::max(1, std::min(256, K / 256));
         kps = ((K + splits - 1) / splits + kTcKC - 1) / kTcKC * kTcKC;
         splits = (K + kps - 1) / kps;
     }
     const int mode = split ? 1 : (accumulate ? 2 : 0);
-    const int nt = N <= 16 ? 16 : (N <= 32 ? 32 : (N <= 64 ? 64 : 128));
+    int nt = N <= 16 ? 16 : (N <= 32 ? 32 : (N <= 64 ? 64 : 128));
+    const int m_tiles = (M + kTcM - 1) / kTcM;
+    while (nt > 32 && m_tiles * ((N + nt - 1) / nt) * splits < 128) nt /= 2;
     dim3 grid((N + nt - 1) / nt, (M + kTcM - 1) / kTcM, splits);
     if (nt == 16)
         k_gemm_tc<16><<<grid, 128, 0, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, kps, mode, err);
