@@ -268,6 +268,9 @@ GS_API int gs_count_dominant(gs_ctx* ctx, const gs_camera* cams_host, int n_view
 #define GS_N_PHASES 8
 /* enable != 0 starts recording (discarding earlier records); 0 stops. */
 GS_API int gs_timing_enable(gs_ctx* ctx, int enable);
+/* Time only the phases whose bit is set in mask (bit p = phase p); fewer event
+ * records in a replayed iteration disturb it less. Clears earlier records. */
+GS_API int gs_timing_phases(gs_ctx* ctx, uint32_t mask);
 /* Synchronise on the recorded events and write, per phase, the summed
  * milliseconds (ms_host[GS_N_PHASES]) and the number of recorded intervals
  * (counts_host[GS_N_PHASES], may be NULL); clears the records. */

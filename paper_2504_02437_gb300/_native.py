@@ -60,6 +60,7 @@ SIGNATURES = {
     "gs_step": (_I, [_P, _P]),
     "gs_iterate": (_I, [_P, C.POINTER(gs_camera), _I, _P, _P, _P, _P]),
     "gs_count_dominant": (_I, [_P, C.POINTER(gs_camera), _I, _P]),
+    "gs_timing_phases": (_I, [_P, C.c_uint32]),
     "gs_insert": (_I, [_P, C.POINTER(gs_camera), _P, _P, _I, C.POINTER(_I), _P, _P]),
     "gs_densify": (_I, [_P, _P, C.POINTER(_I), _P]),
     "gs_debug_projection": (_I, [_P, _I, _P]),

@@ -200,8 +200,16 @@ class GaussianMap:
         return n.value
 
     # ---- timing
-    def timing(self, enable: bool = True):
-        self._check(self.lib.gs_timing_enable(self.ctx, 1 if enable else 0))
+    def timing(self, enable: bool = True, phases=None):
+        """Start (discarding earlier records) or stop per-phase device timing; ``phases`` (names of
+        ``PHASES``) restricts it to those phases."""
+        if enable and phases is not None:
+            mask = 0
+            for name in phases:
+                mask |= 1 << N.PHASES.index(name)
+            self._check(self.lib.gs_timing_phases(self.ctx, mask))
+        else:
+            self._check(self.lib.gs_timing_enable(self.ctx, 1 if enable else 0))
 
     def timing_read(self) -> dict:
         """Summed device milliseconds and interval counts per phase since timing was enabled."""

@@ -33,10 +33,12 @@ int fail(gs_ctx* c, int code, const char* what, cudaError_t e = cudaSuccess) {
 struct CamBatch {
     DevCamera cam[GS_MAX_VIEWS];
     int n;
+    const float* target;   // the iteration's target image (read through the context's target slot)
 };
 
-__global__ void k_set_cams(CamBatch b, DevCamera* dst) {
+__global__ void k_set_cams(CamBatch b, DevCamera* dst, const float** target_slot) {
     int i = threadIdx.x;
+    if (i == 0 && target_slot != nullptr) *target_slot = b.target;
     if (i < b.n) dst[i] = b.cam[i];
 }
 
@@ -187,7 +189,7 @@ int setup_views(gs_ctx* c, const gs_camera* cams, int n_views, cudaStream_t s) {
     int code = prepare_views(c, cams, n_views, b);
     if (code != GS_OK) return code;
     ++c->launches;
-    k_set_cams<<<1, 32, 0, s>>>(b, c->dcam);
+    k_set_cams<<<1, 32, 0, s>>>(b, c->dcam, c->target_slot);
     CK(cudaGetLastError());
     return GS_OK;
 }
@@ -209,7 +211,7 @@ struct Phase {
     cudaStream_t s;
     cudaEvent_t end = nullptr;
     Phase(gs_ctx* c_, int id, cudaStream_t s_) : c(c_), s(s_) {
-        if (!c->timing) return;
+        if (!(c->timing & (1u << id))) return;
         cudaEvent_t a = take_event(c);
         end = take_event(c);
         if (!a || !end) {
@@ -367,6 +369,7 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         ok = ok && dalloc(&c->grad2d, kGrad2dStride * V * cap) == cudaSuccess;
         ok = ok && dalloc(&c->hist, (size_t)256 * c->sort_blocks + 256) == cudaSuccess;
         ok = ok && dalloc(&c->dcount, 8) == cudaSuccess;
+        ok = ok && dalloc(&c->target_slot, 1) == cudaSuccess;
         if (cfg->lambda_photo > 0.f) {
             ok = ok && dalloc(&c->ssim_maps, (size_t)3 * 3 * V * maxpix) == cudaSuccess;
             ok = ok && dalloc(&c->ssim_part, (size_t)2 * ssim_blocks(cfg->max_width, cfg->max_height,
@@ -414,7 +417,7 @@ void gs_destroy(gs_ctx* c) {
     for (auto e : c->tpool) cudaEventDestroy(e);
     void* ptrs[] = {c->params, c->grads, c->adam_m, c->adam_v, c->dens_sum, c->dens_cnt, c->dom_cnt, c->adam_pw, c->dcam, c->rec,
                     c->tiles_touched, c->depth, c->dkey[0], c->dkey[1], c->dval[0], c->dval[1], c->offsets, c->ranges,
-                    c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->ssim_maps, c->ssim_part, c->dcount,
+                    c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, (void*)c->target_slot, c->ssim_maps, c->ssim_part, c->dcount,
                     c->partials, c->fpart,
                     c->own_rgb};
     for (void* p : ptrs) cudaFree(p);
@@ -526,7 +529,7 @@ int gs_loss(gs_ctx* c, const float* target, float* loss_dev, void* stream) {
     const DevConst k = dev_const(c->cfg);
     Phase ph(c, GS_PHASE_LOSS, s);
     if (c->cfg.lambda_photo > 0.f) {
-        CK(launch_ssim_loss(c, k, c->rendered_rgb, target, c->ssim_part, s));
+        CK(launch_ssim_loss(c, k, c->rendered_rgb, target, nullptr, c->ssim_part, s));
         CK(launch_loss_tail(c, k, c->ssim_part, 2 * ssim_blocks(c->width, c->height, c->n_views), out, s));
     } else {
         CK(launch_loss(c, k, c->rendered_rgb, target, out, s));
@@ -579,8 +582,8 @@ static int autotune(gs_ctx* c, const gs_camera* cams, int n_views, const float* 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    const bool timing = c->timing;
-    c->timing = false;
+    const uint32_t timing = c->timing;
+    c->timing = 0;
     float best = 1e30f;
     int bt = 16, bp = 1, code = GS_OK;
     for (const auto& cd : cand) {
@@ -599,7 +602,8 @@ static int autotune(gs_ctx* c, const gs_camera* cams, int n_views, const float* 
                     cudaSuccess)
                 code = GS_ERR_CUDA;
             int fgrid = 0;
-            if (code == GS_OK && launch_raster_fused(c, k, target, rgb, c->fpart, c->n_fpart, &fgrid, s) != cudaSuccess)
+            if (code == GS_OK &&
+                launch_raster_fused(c, k, target, nullptr, rgb, c->fpart, c->n_fpart, &fgrid, s) != cudaSuccess)
                 code = GS_ERR_CUDA;
             cudaEventRecord(e1, s);
             if (cudaEventSynchronize(e1) != cudaSuccess) code = GS_ERR_CUDA;
@@ -666,12 +670,14 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
     if (code != GS_OK) return code;
     const bool same = c->graph && c->graph_views == n_views && c->graph_w == cams[0].width &&
                       c->graph_h == cams[0].height && c->graph_n == c->n && c->graph_tile == c->tile &&
-                      c->graph_ppt == c->ppt && c->graph_pair_cap == c->pair_cap && c->graph_target == target &&
+                      c->graph_ppt == c->ppt && c->graph_pair_cap == c->pair_cap &&
                       c->graph_loss == loss_out && c->graph_rgb == rgb && c->graph_timing == c->timing;
     if (same) {
         // replay: new cameras go in as the upload kernel's parameters
         DevCamera* dst = c->dcam;
-        void* args[2] = {&b, &dst};
+        const float** slot = c->target_slot;
+        b.target = target;   // the graph reads the target through the slot: any buffer per call
+        void* args[3] = {&b, &dst, &slot};
         cudaKernelNodeParams kp = {};
         kp.func = (void*)k_set_cams;
         kp.gridDim = dim3(1);
@@ -731,7 +737,8 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
     {
         DevCamera* dst = c->dcam;
         ++c->launches;
-        k_set_cams<<<1, 32, 0, cs>>>(b, dst);
+        b.target = target;
+        k_set_cams<<<1, 32, 0, cs>>>(b, dst, c->target_slot);
         cc = front_half(c, k, cs);
         const bool ssim = c->cfg.lambda_photo > 0.f;
         // with the SSIM term dL/dC needs the whole image: forward, loss, adjoint as three kernels;
@@ -739,7 +746,7 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
         if (cc == GS_OK) cc = back_half(c, k, ssim ? rgb : nullptr, nullptr, cs);
         if (cc == GS_OK && ssim) {
             Phase ph(c, GS_PHASE_LOSS, cs);
-            if (launch_ssim_loss(c, k, rgb, target, c->ssim_part, cs) != cudaSuccess ||
+            if (launch_ssim_loss(c, k, rgb, target, c->target_slot, c->ssim_part, cs) != cudaSuccess ||
                 launch_loss_tail(c, k, c->ssim_part, 2 * ssim_blocks(c->width, c->height, c->n_views), loss_out,
                                  cs) != cudaSuccess)
                 cc = GS_ERR_CUDA;
@@ -754,7 +761,8 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
             int fgrid = 0;
             {
                 Phase ph(c, GS_PHASE_RASTER_FUSED, cs);
-                if (launch_raster_fused(c, k, target, rgb, c->fpart, c->n_fpart, &fgrid, cs) != cudaSuccess)
+                if (launch_raster_fused(c, k, target, c->target_slot, rgb, c->fpart, c->n_fpart, &fgrid, cs) !=
+                    cudaSuccess)
                     cc = GS_ERR_CUDA;
             }
             if (cc == GS_OK) {
@@ -837,7 +845,14 @@ int gs_timing_enable(gs_ctx* c, int enable) {
         c->tpool.push_back(r.b);
     }
     c->trec.clear();
-    c->timing = enable != 0;
+    c->timing = enable != 0 ? (1u << GS_N_PHASES) - 1u : 0u;
+    return GS_OK;
+}
+
+int gs_timing_phases(gs_ctx* c, uint32_t mask) {
+    const int code = gs_timing_enable(c, 0);
+    if (code != GS_OK) return code;
+    c->timing = mask & ((1u << GS_N_PHASES) - 1u);
     return GS_OK;
 }
 

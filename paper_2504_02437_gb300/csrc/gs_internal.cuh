@@ -109,6 +109,7 @@ struct gs_ctx {
 
     // scratch
     uint32_t* hist = nullptr;               // radix / scan block counters
+    const float** target_slot = nullptr;    // device: the target image of the current iteration
     float* ssim_maps = nullptr;             // [3][V][3][H][W] SSIM derivative maps (lambda_photo > 0)
     float* ssim_part = nullptr;             // [2 ssim_blocks] per-CTA photometric loss terms
     int sort_blocks = 0;
@@ -127,7 +128,7 @@ struct gs_ctx {
     cudaGraphExec_t graph = nullptr;
     cudaGraph_t graph_src = nullptr;        // kept alive: exec updates address its nodes
     int graph_views = 0, graph_w = 0, graph_h = 0, graph_n = 0, graph_tile = 0, graph_ppt = 0;
-    bool graph_timing = false;
+    uint32_t graph_timing = 0;
     int64_t graph_pair_cap = 0;
     const float* graph_target = nullptr;
     float* graph_loss = nullptr;
@@ -152,7 +153,7 @@ struct gs_ctx {
     float* own_rgb = nullptr;               // internal image when the caller gives none
     size_t own_rgb_elems = 0;
     // phase timing (gs_timing_enable / gs_timing_read)
-    bool timing = false;
+    uint32_t timing = 0;                 // bit p: phase p is timed
     struct TimingRec {
         int phase;
         cudaEvent_t a, b;
@@ -187,8 +188,8 @@ cudaError_t launch_raster_backward(gs_ctx* c, const DevConst& k, const float* dL
 cudaError_t launch_count_work(gs_ctx* c, const DevConst& k, unsigned long long* out, cudaStream_t s);
 // forward + L1 loss + adjoint of every (view, tile) in one persistent launch; writes the image,
 // the screen-space gradients and one photometric partial per CTA (at most max_grid CTAs)
-cudaError_t launch_raster_fused(gs_ctx* c, const DevConst& k, const float* target, float* rgb, float* partials,
-                                int max_grid, int* grid_out, cudaStream_t s);
+cudaError_t launch_raster_fused(gs_ctx* c, const DevConst& k, const float* target, const float* const* target_slot,
+                                float* rgb, float* partials, int max_grid, int* grid_out, cudaStream_t s);
 // planar term partials + the final fixed-order sum of photometric and planar partials
 cudaError_t launch_loss_tail(gs_ctx* c, const DevConst& k, const float* photo_partials, int n_photo,
                              float* loss_out, cudaStream_t s);
@@ -196,8 +197,8 @@ cudaError_t launch_loss(gs_ctx* c, const DevConst& k, const float* rgb, const fl
                         cudaStream_t s);
 cudaError_t launch_adam(gs_ctx* c, cudaStream_t s);
 int ssim_blocks(int width, int height, int n_views);
-cudaError_t launch_ssim_loss(gs_ctx* c, const DevConst& k, const float* rgb, const float* target, float* partials,
-                             cudaStream_t s);
+cudaError_t launch_ssim_loss(gs_ctx* c, const DevConst& k, const float* rgb, const float* target,
+                             const float* const* target_slot, float* partials, cudaStream_t s);
 
 // Adam (bias-corrected) with one learning rate per parameter row.
 struct AdamArgs {

@@ -514,9 +514,10 @@ template <int TILE, int PPT>
 __global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
     k_raster_fused(const uint2* __restrict__ ranges, const uint32_t* __restrict__ pval,
                    const float4* __restrict__ rec, int width, int height, int tiles_x, int tiles_per_view,
-                   DevConst kc, const float* __restrict__ target, float scale, float* __restrict__ out_rgb,
-                   float* __restrict__ grad2d, float* __restrict__ partials, uint32_t* __restrict__ queue,
-                   uint32_t n_items, const uint32_t* __restrict__ order) {
+                   DevConst kc, const float* __restrict__ target, const float* const* __restrict__ target_slot,
+                   float scale, float* __restrict__ out_rgb, float* __restrict__ grad2d, float* __restrict__ partials,
+                   uint32_t* __restrict__ queue, uint32_t n_items, const uint32_t* __restrict__ order) {
+    if (target_slot != nullptr) target = *target_slot;   // a replayed graph's per-call target
     int bin;
     const size_t HW = (size_t)width * height;
     float loss = 0.f;
@@ -660,14 +661,15 @@ static void bwd_launch(gs_ctx* c, const DevConst& k, const float* dLdC, cudaStre
 }
 
 template <int TILE, int PPT>
-static void fused_launch(gs_ctx* c, const DevConst& k, const float* target, float* rgb, cudaStream_t s, int tpv,
-                         float* partials, int max_grid, int* grid_out) {
+static void fused_launch(gs_ctx* c, const DevConst& k, const float* target, const float* const* target_slot,
+                         float* rgb, cudaStream_t s, int tpv, float* partials, int max_grid, int* grid_out) {
     constexpr int NT = Layout<TILE, PPT>::kThreads;
     const int grid = std::min(std::min(resident_grid<3, TILE, PPT>(k_raster_fused<TILE, PPT>, NT, c->num_sms),
                                        c->n_bins), max_grid);
     const float scale = k.lambda_color / (float)(3 * (size_t)c->width * c->height);
     k_raster_fused<TILE, PPT><<<grid, NT, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width, c->height,
-                                                  c->hcam[0].tiles_x, tpv, k, target, scale, rgb, c->grad2d, partials,
+                                                  c->hcam[0].tiles_x, tpv, k, target, target_slot, scale, rgb,
+                                                  c->grad2d, partials,
                                                   c->dcount + 6, (uint32_t)c->n_bins, nullptr);
     *grid_out = grid;
 }
@@ -704,15 +706,15 @@ cudaError_t launch_raster_backward(gs_ctx* c, const DevConst& k, const float* dL
     return cudaGetLastError();
 }
 
-cudaError_t launch_raster_fused(gs_ctx* c, const DevConst& k, const float* target, float* rgb, float* partials,
-                                int max_grid, int* grid_out, cudaStream_t s) {
+cudaError_t launch_raster_fused(gs_ctx* c, const DevConst& k, const float* target, const float* const* target_slot,
+                                float* rgb, float* partials, int max_grid, int* grid_out, cudaStream_t s) {
     const int tpv = c->hcam[0].tiles_x * c->hcam[0].tiles_y;
     *grid_out = 0;
     if (c->n_bins == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(c->dcount + 6, 0, sizeof(uint32_t), s);   // work queue
     if (e != cudaSuccess) return e;
     ++c->launches;
-    GS_DISPATCH(fused_launch, c, k, target, rgb, s, tpv, partials, max_grid, grid_out);
+    GS_DISPATCH(fused_launch, c, k, target, target_slot, rgb, s, tpv, partials, max_grid, grid_out);
     return cudaGetLastError();
 }
 

@@ -52,13 +52,14 @@ __device__ __forceinline__ void stage_plane(const float* __restrict__ src, int W
 }
 
 __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const float* __restrict__ x, const float* __restrict__ y,
-                                                           int W, int H, SsimWindow win, float neg_scale,
+                                                           const float* const* __restrict__ y_slot, int W, int H, SsimWindow win, float neg_scale,
                                                            float constant, float* __restrict__ d_mu,
                                                            float* __restrict__ d_xx, float* __restrict__ d_xy,
                                                            float* __restrict__ partials) {
     __shared__ float sx[kSsimSpan][kSsimSpan], sy[kSsimSpan][kSsimSpan];
     __shared__ float hb[5][kSsimSpan][kSsimTile];
     __shared__ float red[kSsimThreads / 32];
+    if (y_slot != nullptr) y = *y_slot;   // a replayed graph's per-call target
     const int plane = blockIdx.z;
     const size_t HW = (size_t)W * H, off = (size_t)plane * HW;
     const int x0 = blockIdx.x * kSsimTile, y0 = blockIdx.y * kSsimTile;
@@ -122,7 +123,8 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_fwd(const float* __restri
 }
 
 __global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const float* __restrict__ x, const float* __restrict__ y,
-                                                           int W, int H, SsimWindow win,
+                                                           const float* const* __restrict__ y_slot, int W, int H,
+                                                           SsimWindow win,
                                                            const float* __restrict__ d_mu,
                                                            const float* __restrict__ d_xx,
                                                            const float* __restrict__ d_xy, float l1_scale,
@@ -131,6 +133,7 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim_bwd(const float* __restri
     __shared__ float sg[3][kSsimSpan][kSsimSpan];
     __shared__ float hb[3][kSsimSpan][kSsimTile];
     __shared__ float red[kSsimThreads / 32];
+    if (y_slot != nullptr) y = *y_slot;
     const int plane = blockIdx.z;
     const size_t HW = (size_t)W * H, off = (size_t)plane * HW;
     const int x0 = blockIdx.x * kSsimTile, y0 = blockIdx.y * kSsimTile;
@@ -197,8 +200,8 @@ int ssim_blocks(int width, int height, int n_views) {
 
 // L_color with the SSIM term for the rendered views: writes dL/dC and, into
 // `partials` (2 ssim_blocks entries), the photometric loss as per-CTA terms.
-cudaError_t launch_ssim_loss(gs_ctx* c, const DevConst& k, const float* rgb, const float* target, float* partials,
-                             cudaStream_t s) {
+cudaError_t launch_ssim_loss(gs_ctx* c, const DevConst& k, const float* rgb, const float* target,
+                             const float* const* target_slot, float* partials, cudaStream_t s) {
     const int W = c->width, H = c->height, V = c->n_views;
     const float lp = c->cfg.lambda_photo;
     const float inv = 1.f / (float)(3 * (size_t)W * H);
@@ -209,9 +212,9 @@ cudaError_t launch_ssim_loss(gs_ctx* c, const DevConst& k, const float* rgb, con
     const int nb = ssim_blocks(W, H, V);
     const SsimWindow win = make_window();
     c->launches += 2;
-    k_ssim_fwd<<<grid, kSsimThreads, 0, s>>>(rgb, target, W, H, win, -ssim_scale, k.lambda_color * lp * (float)V,
+    k_ssim_fwd<<<grid, kSsimThreads, 0, s>>>(rgb, target, target_slot, W, H, win, -ssim_scale, k.lambda_color * lp * (float)V,
                                              d_mu, d_xx, d_xy, partials);
-    k_ssim_bwd<<<grid, kSsimThreads, 0, s>>>(rgb, target, W, H, win, d_mu, d_xx, d_xy, l1_scale, ssim_scale,
+    k_ssim_bwd<<<grid, kSsimThreads, 0, s>>>(rgb, target, target_slot, W, H, win, d_mu, d_xx, d_xy, l1_scale, ssim_scale,
                                              c->dLdC, partials + nb);
     return cudaGetLastError();
 }
