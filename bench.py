@@ -182,13 +182,16 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def dist_setup():
+def dist_setup(backend: str = "nccl"):
+    """Rank, world size and local rank from the launcher's environment; joins the process group
+    when there is more than one rank (nccl on GPUs, gloo for CPU ranks)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
     return world, rank, local
 
 
@@ -199,13 +202,20 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """The largest value over the ranks (the slowest rank's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(steps: int, world: int, slowest_ms: float) -> float:
+    """Whole-job iterations/s of `world` replicas that each ran `steps` iterations, timed by the slowest."""
+    return world * steps / (slowest_ms / 1000.0)
 
 
 # --------------------------------------------------------------------------- CPU oracle
@@ -321,7 +331,7 @@ def run_ours(args):
     total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     total_ms = max_over_ranks(total_ms, world)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1000.0)
+    value = replica_throughput(args.steps, world, total_ms)
     final_loss = loss.cpu().numpy().tolist()
 
     # ---- end to end through the API: each step's target goes up from pinned host memory and its
@@ -365,7 +375,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(world)
     e2e_ms = max_over_ranks(e_start.elapsed_time(e_end), world)
-    e2e_value = world * args.steps / (e2e_ms / 1000.0)
+    e2e_value = replica_throughput(args.steps, world, e2e_ms)
 
     # ---- roofline of the dominant kernel
     work = gm.debug_work()
