@@ -27,6 +27,15 @@ def _ptr(t: Optional[torch.Tensor]) -> Optional[C.c_void_p]:
     return C.c_void_p(t.data_ptr())
 
 
+def _f32(t: Optional[torch.Tensor], shape: tuple, name: str) -> Optional[torch.Tensor]:
+    """A float32 CUDA tensor of the given shape, passed without a copy (None stays None)."""
+    if t is None:
+        return None
+    if t.dtype != torch.float32 or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected float32 {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+    return t
+
+
 def to_gs_camera(cam) -> N.gs_camera:
     """Any object with width, height, fx, fy, cx, cy, R (3x3 world->camera) and t."""
     g = N.gs_camera()
@@ -166,6 +175,9 @@ class GaussianMap:
         arr, V, H, W = _cams(cams)
         if loss_out is None:
             loss_out = torch.empty(3, device=f"cuda:{self.device}", dtype=torch.float32)
+        target = _f32(target, (V, 3, H, W), "target")
+        _f32(loss_out, (3,), "loss_out")
+        _f32(rgb_out, (V, 3, H, W), "rgb_out")
         self._check(self.lib.gs_iterate(self.ctx, arr, V, _ptr(target), _ptr(loss_out), _ptr(rgb_out), _stream()))
         return loss_out
 

@@ -831,7 +831,6 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
     c->graph_tile = c->tile;
     c->graph_ppt = c->ppt;
     c->graph_pair_cap = c->pair_cap;
-    c->graph_target = target;
     c->graph_loss = loss_out;
     c->graph_rgb = rgb;
     c->graph_timing = c->timing;

@@ -130,7 +130,6 @@ struct gs_ctx {
     int graph_views = 0, graph_w = 0, graph_h = 0, graph_n = 0, graph_tile = 0, graph_ppt = 0;
     uint32_t graph_timing = 0;
     int64_t graph_pair_cap = 0;
-    const float* graph_target = nullptr;
     float* graph_loss = nullptr;
     float* graph_rgb = nullptr;
     cudaStream_t cap_stream = nullptr;      // stream the iteration is captured on
