@@ -18,10 +18,10 @@ constexpr int kRecFloat4 = 3;       // float4 per (view, Gaussian) raster record
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
-// Camera as the kernels read it (one per view, in device memory).
 // largest pair buffer (pair indices are 32-bit)
 constexpr int64_t kMaxPairs = 0xFFFFFFF0ll;
 
+// Camera as the kernels read it (one per view, in device memory).
 struct DevCamera {
     float R[9];
     float t[3];
@@ -206,12 +206,13 @@ struct AdamArgs {
 };
 AdamArgs adam_args(const gs_ctx* c);
 
+// inv_bc1, inv_bc2: reciprocals of the bias corrections 1 - beta^t (rounded once from float64)
 __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& v, float lr, const AdamArgs& a,
-                                            float bc1, float bc2) {
+                                            float inv_bc1, float inv_bc2) {
     m = a.b1 * m + (1.f - a.b1) * g;
     v = a.b2 * v + (1.f - a.b2) * g * g;
-    const float mh = m / bc1, vh = v / bc2;
-    p -= lr * mh / (sqrtf(vh) + a.eps);
+    const float mh = m * inv_bc1, vh = v * inv_bc2;
+    p -= __fdividef(lr * mh, sqrtf(vh) + a.eps);   // denominator < 2^126: 2-ulp division
 }
 
 // Bias corrections of the next Adam step from device state (so that a graph
@@ -219,13 +220,14 @@ __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& 
 // t = st[4] completed steps; st[1] = pair-buffer overflow flag (step skipped).
 // Thread 0 of every CTA reads them before taking a ticket (st[2]); the last
 // CTA of the launch advances pw and t, so every CTA uses the same t + 1.
+// sbc = {1 / (1 - beta1^(t+1)), 1 / (1 - beta2^(t+1)), 1 if the step is skipped}.
 __device__ __forceinline__ void adam_bias_begin(const AdamArgs& a, const uint32_t* st, const double* pw,
                                                 float* sbc, double* spw) {
     const double p1 = pw[0] * (double)a.b1, p2 = pw[1] * (double)a.b2;
     spw[0] = p1;
     spw[1] = p2;
-    sbc[0] = (float)(1.0 - p1);
-    sbc[1] = (float)(1.0 - p2);
+    sbc[0] = (float)(1.0 / (1.0 - p1));
+    sbc[1] = (float)(1.0 / (1.0 - p2));
     sbc[2] = st[1] != 0u ? 1.f : 0.f;
 }
 __device__ __forceinline__ void adam_bias_end(uint32_t* st, double* pw, const float* sbc, const double* spw,

@@ -71,6 +71,35 @@ __device__ __forceinline__ void stage_record(const float4* __restrict__ rec, uin
     s2 = make_float4(c.x, c.y, c.z, thr);
 }
 
+// The same ellipse's extent across its long axis: with Q = -(a' dx^2 + b' dx dy + c' dy^2)
+// = d^T M d, the set Q <= -thr has half-width sqrt(-thr / lambda_max(M)) along the unit
+// eigenvector n of lambda_max(M) (the ellipse's short axis), enlarged by the same margin as the
+// box. A pixel block whose projection on n lies farther from the mean cannot blend; for an
+// elongated, rotated ellipse this strip cuts much of its axis-aligned box.
+__device__ __forceinline__ void short_axis_strip(const float4 s1, float thr, float& nx, float& ny, float& wn) {
+    nx = 1.f;
+    ny = 0.f;
+    wn = 3.0e38f;
+    const float A = -s1.x, B2 = -0.5f * s1.y, C = -s1.z;   // M = [[A, B2], [B2, C]]
+    if (!(thr <= 0.f)) return;
+    const float half = 0.5f * (A - C);
+    const float lam = 0.5f * (A + C) + sqrtf(half * half + B2 * B2);
+    if (!(lam > 0.f)) return;
+    // eigenvector of lam: the better conditioned of (B2, lam - A) and (lam - C, B2)
+    float ex = B2, ey = lam - A;
+    const float fx = lam - C, fy = B2;
+    if (fx * fx + fy * fy > ex * ex + ey * ey) {
+        ex = fx;
+        ey = fy;
+    }
+    const float nn = ex * ex + ey * ey;
+    if (!(nn > 0.f)) return;
+    const float inv = rsqrtf(nn);
+    nx = ex * inv;
+    ny = ey * inv;
+    wn = fmaf(sqrtf(-thr / lam), 1.001f, 0.01f);
+}
+
 // Thread layout of a TILE x TILE tile: each thread owns PPT pixels of one
 // column, 4 rows apart; warp w owns an 8 x (4 PPT) block.
 template <int TILE, int PPT>
@@ -195,9 +224,15 @@ struct TileGeom {
     __device__ int py(int p) const { return py0 + 4 * p; }
 };
 
-// Warps of the CTA whose 8 x (4 PPT) pixel block meets the box u +- hx, v +- hy.
+// Warps of the CTA whose 8 x (4 PPT) pixel block meets the box u +- hx, v +- hy and the
+// short-axis strip |n . (x - u)| <= wn.
 template <int TILE, int PPT>
-__device__ __forceinline__ uint32_t warp_mask(const TileGeom<TILE, PPT>& g, const float4 s0) {
+__device__ __forceinline__ uint32_t warp_mask(const TileGeom<TILE, PPT>& g, const float4 s0, const float4 s1,
+                                              float thr) {
+    float nx, ny, wn;
+    short_axis_strip(s1, thr, nx, ny, wn);
+    // half-extents of a warp's pixel block projected on n, plus the rounding slack of the box test
+    const float hb = 3.5f * fabsf(nx) + 0.5f * (float)(4 * PPT - 1) * fabsf(ny) + wn + 0.01f;
     constexpr int NW = Layout<TILE, PPT>::kThreads / 32;
     constexpr int BX = Layout<TILE, PPT>::kBlocksX;
     const float tox = (float)(g.txi * TILE) - g.ox, toy = (float)(g.tyi * TILE) - g.oy;
@@ -208,7 +243,8 @@ __device__ __forceinline__ uint32_t warp_mask(const TileGeom<TILE, PPT>& g, cons
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
         const float bx = tox + 8.f * (float)(w % BX), by = toy + (float)(4 * PPT) * (float)(w / BX);
-        const bool hit = x0 <= bx + 7.f && x1 >= bx && y0 <= by + (float)(4 * PPT - 1) && y1 >= by;
+        const float sc = nx * (bx + 3.5f - s0.x) + ny * (by + 0.5f * (float)(4 * PPT - 1) - s0.y);
+        const bool hit = x0 <= bx + 7.f && x1 >= bx && y0 <= by + (float)(4 * PPT - 1) && y1 >= by && fabsf(sc) <= hb;
         m |= hit ? (1u << w) : 0u;
     }
     return m;
@@ -252,7 +288,7 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
                 const uint32_t item = pval[j];
                 stage_record(rec, item, g.ox, g.oy, kc.alpha_min, s0[i], s1[i], s2[i]);
                 sid[i] = item;
-                st.mask[i] = warp_mask<TILE, PPT>(g, s0[i]);
+                st.mask[i] = warp_mask<TILE, PPT>(g, s0[i], s1[i], s2[i].w);
             }
         }
         __syncthreads();
@@ -348,7 +384,7 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
                 const uint32_t item = pval[j];
                 stage_record(rec, item, g.ox, g.oy, kc.alpha_min, s0[i], s1[i], s2[i]);
                 sid[i] = item;
-                st.mask[i] = warp_mask<TILE, PPT>(g, s0[i]);
+                st.mask[i] = warp_mask<TILE, PPT>(g, s0[i], s1[i], s2[i].w);
             }
         }
         __syncthreads();

@@ -109,8 +109,8 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, const float
     if (threadIdx.x == 0) adam_bias_begin(a, st, pw, sbc, spw);
     __syncthreads();
     if (sbc[2] == 0.f) {
-        const float bc1 = sbc[0], bc2 = sbc[1];
-        auto upd = [&](float& p, float g, float& m, float& v, float lr) { adam_update(p, g, m, v, lr, a, bc1, bc2); };
+        const float ibc1 = sbc[0], ibc2 = sbc[1];   // 1 / (1 - beta^t)
+        auto upd = [&](float& p, float g, float& m, float& v, float lr) { adam_update(p, g, m, v, lr, a, ibc1, ibc2); };
         // grid-stride over the 14 rows x ceil(n / 4) groups of 4 parameters
         const uint32_t nvec = (uint32_t)(n + 3) / 4u, total = nvec * (uint32_t)kParamRows;
         for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {

@@ -360,3 +360,44 @@ def test_iterate_replay_follows_a_new_target_buffer(scene):
     assert abs(la[1] - la[0]) > 1e-3 * la[0]          # the two targets give different losses
     d = np.abs(ga.params().cpu().numpy() - gb.params().cpu().numpy())
     assert np.median(d) < 1e-7
+
+
+def test_pair_buffer_grows_in_render(scene, ref):
+    """A render that needs more (view, tile, Gaussian) pairs than the buffer holds grows it first:
+    the image still matches the oracle."""
+    p, cam, _ = scene
+    fwd, _ = ref
+    gm = new_map(p.shape[1], pair_capacity=64)
+    gm.set_params(cuda(p))
+    rgb = gm.render(cam).cpu().numpy()[0]
+    err = np.abs(rgb - fwd["rgb"]).max(axis=0)
+    assert err[~fwd["near"]].max() <= IMG_ATOL
+
+
+def test_pair_overflow_in_a_replay_skips_the_step_and_grows(scene):
+    """A replayed iteration whose new camera needs more pairs than the buffer sized at capture
+    skips its Adam step (flagged on the device); the next call reports GS_ERR_CAPACITY with the
+    buffer grown, and the following calls iterate normally."""
+    from paper_2504_02437_gb300._native import GSError, GS_ERR_CAPACITY
+    p, cam, tg = scene
+    far = rotated_cam(cam, [0.0, 0.0, 0.0], [0.0, 0.0, -6.0])      # sees a handful of Gaussians
+    near_view = cam                                                # sees all of them
+    gm = new_map(p.shape[1], pair_capacity=64, tile_size=16, pixels_per_thread=1)
+    gm.set_params(cuda(p))
+    tgt = cuda(tg)
+    loss = torch.empty(3, device="cuda")
+    gm.iterate(far, tgt, loss)          # direct call: sizes the pair buffer for `far`, captures
+    gm.iterate(far, tgt, loss)          # replay
+    torch.cuda.synchronize()
+    before = gm.params().cpu().numpy()
+    gm.iterate(near_view, tgt, loss)    # replay with far more pairs: overflows, step skipped
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(gm.params().cpu().numpy(), before)
+    with pytest.raises(GSError) as e:
+        gm.iterate(near_view, tgt, loss)
+    assert e.value.code == GS_ERR_CAPACITY
+    gm.iterate(near_view, tgt, loss)    # grown: a direct call and a new capture
+    gm.iterate(near_view, tgt, loss)
+    torch.cuda.synchronize()
+    assert not np.array_equal(gm.params().cpu().numpy(), before)
+    assert np.isfinite(gm.params().cpu().numpy()).all()
