@@ -241,9 +241,11 @@ int front_half(gs_ctx* c, const DevConst& k, cudaStream_t s) {
     const uint32_t items = (uint32_t)c->n_views * (uint32_t)c->n;
     Phase ph(c, GS_PHASE_PROJECT, s);
     CK(launch_preprocess(c, c->n_views, k, s));
+    // the visible items, compacted in item order, sorted by depth (dcount[8] of them)
     int buf = 0;
-    CK(radix_sort_pairs(c, c->dkey, c->dval, c->dcount + 3, items, items, 32, &buf, s));
-    CK(scan_tiles(c, items, s));
+    const uint32_t hint = c->visible_hint ? std::min(c->visible_hint + c->visible_hint / 4 + 256, items) : items;
+    CK(radix_sort_pairs(c, c->dkey, c->dval, c->dcount + 8, items, hint, 32, &buf, s));
+    CK(scan_tiles(c, items, c->dcount + 8, s));
     return GS_OK;
 }
 
@@ -253,7 +255,7 @@ int back_half(gs_ctx* c, const DevConst& k, float* rgb, int32_t* argmax, cudaStr
     {
         Phase ph(c, GS_PHASE_BIN, s);
         CK(cudaMemsetAsync(c->dcount + 1, 0, sizeof(uint32_t), s));
-        CK(emit_pairs(c, items, s));
+        CK(emit_pairs(c, items, c->dcount + 8, s));
         int bits = std::max(1, ceil_log2((uint32_t)c->n_bins));
         CK(radix_sort_pairs(c, c->pkey, c->pval, c->dcount, (uint32_t)std::min<int64_t>(c->pair_cap, 0xFFFFFFFFll),
                             c->pairs_hint, bits, &c->pair_buf, s));
@@ -368,7 +370,8 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         ok = ok && dalloc(&c->dLdC, 3 * V * maxpix) == cudaSuccess;
         ok = ok && dalloc(&c->grad2d, kGrad2dStride * V * cap) == cudaSuccess;
         ok = ok && dalloc(&c->hist, (size_t)256 * c->sort_blocks + 256) == cudaSuccess;
-        ok = ok && dalloc(&c->dcount, 8) == cudaSuccess;
+        ok = ok && dalloc(&c->dcount, 16) == cudaSuccess;
+        ok = ok && dalloc(&c->vis_blocks, V * ((cap + 255) / 256) + 1) == cudaSuccess;
         ok = ok && dalloc(&c->target_slot, 1) == cudaSuccess;
         if (cfg->lambda_photo > 0.f) {
             ok = ok && dalloc(&c->ssim_maps, (size_t)3 * 3 * V * maxpix) == cudaSuccess;
@@ -379,12 +382,12 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         c->n_fpart = 32 * c->num_sms;   // at most 32 resident CTAs per SM
         ok = ok && dalloc(&c->fpart, (size_t)c->n_fpart) == cudaSuccess;
         ok = ok && alloc_pairs(c, pc) == cudaSuccess;
-        ok = ok && cudaMallocHost((void**)&c->hcount, sizeof(uint32_t) * 8) == cudaSuccess;
+        ok = ok && cudaMallocHost((void**)&c->hcount, sizeof(uint32_t) * 16) == cudaSuccess;
         ok = ok && cudaMallocHost((void**)&c->hflags, sizeof(uint32_t) * 4) == cudaSuccess;
         ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&c->graph_done, cudaEventDisableTiming) == cudaSuccess;
         if (!ok) { code = fail(c, GS_ERR_OOM, "device allocation failed"); break; }
-        uint32_t init[8] = {0, 0, 0, 0xFFFFFFFFu, 0, 0, 0, 0};
+        uint32_t init[16] = {0, 0, 0, 0xFFFFFFFFu, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         e = cudaMemcpy(c->dcount, init, sizeof(init), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemset(c->adam_m, 0, sizeof(float) * kParamRows * cap);
         if (e == cudaSuccess) e = cudaMemset(c->adam_v, 0, sizeof(float) * kParamRows * cap);
@@ -417,7 +420,7 @@ void gs_destroy(gs_ctx* c) {
     for (auto e : c->tpool) cudaEventDestroy(e);
     void* ptrs[] = {c->params, c->grads, c->adam_m, c->adam_v, c->dens_sum, c->dens_cnt, c->dom_cnt, c->adam_pw, c->dcam, c->rec,
                     c->tiles_touched, c->depth, c->dkey[0], c->dkey[1], c->dval[0], c->dval[1], c->offsets, c->ranges,
-                    c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, (void*)c->target_slot, c->ssim_maps, c->ssim_part, c->dcount,
+                    c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->vis_blocks, (void*)c->target_slot, c->ssim_maps, c->ssim_part, c->dcount,
                     c->partials, c->fpart,
                     c->own_rgb};
     for (void* p : ptrs) cudaFree(p);
@@ -500,9 +503,10 @@ int gs_render(gs_ctx* c, const gs_camera* cams, int n_views, float* rgb, float* 
     if (c->n == 0) return render_empty(c, rgb, T, argmax, s);
     if ((code = front_half(c, k, s)) != GS_OK) return code;
     // size the pair buffers: read P back (the one synchronisation of a render)
-    CK(cudaMemcpyAsync(c->hcount, c->dcount, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->hcount, c->dcount, sizeof(uint32_t) * 9, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const int64_t P = c->hcount[0];
+    c->visible_hint = c->hcount[8];
     c->pairs_hint = (uint32_t)std::min<int64_t>(P, 0xFFFFFFFFll);
     if (P > c->pair_cap) {
         drop_graph(c);

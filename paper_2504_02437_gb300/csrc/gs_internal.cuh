@@ -113,9 +113,11 @@ struct gs_ctx {
     float* ssim_maps = nullptr;             // [3][V][3][H][W] SSIM derivative maps (lambda_photo > 0)
     float* ssim_part = nullptr;             // [2 ssim_blocks] per-CTA photometric loss terms
     int sort_blocks = 0;
-    uint32_t* dcount = nullptr;             // device scalars [8]: [0] pairs, [1] overflow, [2] Adam
+    uint32_t* dcount = nullptr;             // device scalars [16]: [0] pairs, [1] overflow, [2] Adam
                                             // ticket, [3] UINT32_MAX, [4] Adam steps, [5] totals,
-                                            // [6], [7] work queues
+                                            // [6], [7] work queues, [8] visible (view, Gaussian) items
+    uint32_t* vis_blocks = nullptr;         // visible items per preprocess CTA, then their offsets
+    uint32_t visible_hint = 0;              // host copy of dcount[8] from the last synchronising render
     uint32_t* hcount = nullptr;             // pinned host mirror
     float* partials = nullptr;              // reduction partials
     float* fpart = nullptr;                 // photometric partials of the fused kernel (one per CTA)
@@ -177,8 +179,9 @@ cudaError_t launch_preprocess_backward(gs_ctx* c, const DevConst& k, bool add_re
 // The count is min(*n_dev, n_max); n_hint (host estimate) only sizes the grid.
 cudaError_t radix_sort_pairs(gs_ctx* c, uint32_t** keys, uint32_t** vals, const uint32_t* n_dev, uint32_t n_max,
                              uint32_t n_hint, int bits, int* out_buf, cudaStream_t s);
-cudaError_t scan_tiles(gs_ctx* c, uint32_t n, cudaStream_t s);
-cudaError_t emit_pairs(gs_ctx* c, uint32_t n, cudaStream_t s);
+cudaError_t scan_tiles(gs_ctx* c, uint32_t n_max, const uint32_t* n_dev, cudaStream_t s);
+cudaError_t scan_blocks(uint32_t* a, uint32_t n, uint32_t* total_dev, cudaStream_t s);
+cudaError_t emit_pairs(gs_ctx* c, uint32_t n_items, const uint32_t* n_dev, cudaStream_t s);
 // exclusive scan of n u32 values (in may equal out); the total goes to *total_dev
 cudaError_t scan_u32(gs_ctx* c, const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* total_dev, cudaStream_t s);
 cudaError_t compute_ranges(gs_ctx* c, cudaStream_t s);

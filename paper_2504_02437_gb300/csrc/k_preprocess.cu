@@ -155,14 +155,12 @@ __device__ __forceinline__ void project_one(const float p[kParamRows], const Sha
     o.det = o.A * o.C - o.B * o.B;
 }
 
-__global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ P, int n, int cap,
-                                                    const DevCamera* __restrict__ cams, DevConst kc, int tile,
-                                                    float4* __restrict__ rec, uint32_t* __restrict__ tiles,
-                                                    uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval,
-                                                    float* __restrict__ depth) {
-    int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    int view = blockIdx.y;
-    if (gid >= n) return;
+// Projection of one (view, Gaussian) item; returns whether it is visible (has tiles).
+__device__ __forceinline__ bool preprocess_one(const float* __restrict__ P, int n, int cap, int gid, int view,
+                                               const DevCamera* __restrict__ cams, const DevConst& kc, int tile,
+                                               float4* __restrict__ rec, uint32_t* __restrict__ tiles,
+                                               uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval,
+                                               float* __restrict__ depth) {
     const DevCamera& cam = cams[view];
     size_t item = (size_t)view * n + gid;
     float p[kParamRows];
@@ -210,6 +208,50 @@ __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ P,
     depth[item] = tz32;
     dkey[item] = valid ? __float_as_uint(tz32) : 0xFFFFFFFFu;
     dval[item] = (uint32_t)item;
+    return valid;
+}
+
+// One thread per (view, Gaussian) item; each CTA also writes how many of its 256
+// consecutive items are visible (block_vis[view * gridDim.x + blockIdx.x]), the
+// first step of the order-keeping compaction ahead of the depth sort.
+__global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ P, int n, int cap,
+                                                    const DevCamera* __restrict__ cams, DevConst kc, int tile,
+                                                    float4* __restrict__ rec, uint32_t* __restrict__ tiles,
+                                                    uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval,
+                                                    float* __restrict__ depth, uint32_t* __restrict__ block_vis) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int view = blockIdx.y;
+    bool vis = false;
+    if (gid < n) vis = preprocess_one(P, n, cap, gid, view, cams, kc, tile, rec, tiles, dkey, dval, depth);
+    const int cnt = __syncthreads_count(vis);
+    if (threadIdx.x == 0) block_vis[(size_t)view * gridDim.x + blockIdx.x] = (uint32_t)cnt;
+}
+
+// Order-keeping compaction of the visible items: CTA b (the items of preprocess
+// CTA b) writes its visible keys and values at the scanned offset block_off[b],
+// in item order, so equal depths keep ascending ids through the stable sort.
+__global__ void __launch_bounds__(256) k_compact_visible(const uint32_t* __restrict__ kin,
+                                                         const uint32_t* __restrict__ vin, int n,
+                                                         const uint32_t* __restrict__ block_off,
+                                                         uint32_t* __restrict__ kout, uint32_t* __restrict__ vout) {
+    __shared__ uint32_t wsum[8];
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const size_t item = (size_t)blockIdx.y * n + gid;
+    const uint32_t key = gid < n ? kin[item] : 0xFFFFFFFFu;
+    const bool vis = key != 0xFFFFFFFFu;
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, vis);
+    if (lane == 0) wsum[w] = __popc(bal);
+    __syncthreads();
+    uint32_t pre = 0;
+    for (int k = 0; k < w; ++k) pre += wsum[k];
+    if (vis) {
+        uint32_t lt;
+        asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+        const uint32_t pos = block_off[(size_t)blockIdx.y * gridDim.x + blockIdx.x] + pre + __popc(bal & lt);
+        kout[pos] = key;
+        vout[pos] = vin[item];
+    }
 }
 
 __global__ void __launch_bounds__(128) k_preprocess_backward(
@@ -371,12 +413,18 @@ __global__ void __launch_bounds__(128) k_preprocess_backward(
 
 }  // namespace
 
+// Projection of every (view, Gaussian) item, then the visible items compacted in
+// item order into dkey[0] / dval[0] (their number in dcount[8]).
 cudaError_t launch_preprocess(gs_ctx* c, int n_views, const DevConst& k, cudaStream_t s) {
     if (c->n == 0) return cudaSuccess;
     dim3 grid((c->n + 255) / 256, n_views);
-    ++c->launches;
+    const uint32_t nblocks = grid.x * grid.y;
+    c->launches += 3;
     k_preprocess<<<grid, 256, 0, s>>>(c->params, c->n, c->cap, c->dcam, k, c->tile, c->rec, c->tiles_touched,
-                                       c->dkey[0], c->dval[0], c->depth);
+                                       c->dkey[1], c->dval[1], c->depth, c->vis_blocks);
+    cudaError_t e = scan_blocks(c->vis_blocks, nblocks, c->dcount + 8, s);
+    if (e != cudaSuccess) return e;
+    k_compact_visible<<<grid, 256, 0, s>>>(c->dkey[1], c->dval[1], c->n, c->vis_blocks, c->dkey[0], c->dval[0]);
     return cudaGetLastError();
 }
 

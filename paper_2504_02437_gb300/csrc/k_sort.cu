@@ -236,8 +236,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
 
 __global__ void __launch_bounds__(256) k_tile_block_sums(const uint32_t* __restrict__ order,
                                                          const uint32_t* __restrict__ tiles, uint32_t n,
+                                                         const uint32_t* __restrict__ n_dev,
                                                          uint32_t* __restrict__ bsum) {
     __shared__ uint32_t ws[8];
+    if (n_dev != nullptr) n = umin(n, *n_dev);
     uint32_t begin, end;
     slice_of(n, gridDim.x, blockIdx.x, begin, end);
     uint32_t s = 0;
@@ -255,9 +257,11 @@ __global__ void __launch_bounds__(256) k_tile_block_sums(const uint32_t* __restr
 
 __global__ void __launch_bounds__(256) k_tile_scan(const uint32_t* __restrict__ order,
                                                    const uint32_t* __restrict__ tiles, uint32_t n,
+                                                   const uint32_t* __restrict__ n_dev,
                                                    const uint32_t* __restrict__ bsum, uint32_t* __restrict__ off) {
     __shared__ uint32_t ws[8];
     __shared__ uint32_t carry;
+    if (n_dev != nullptr) n = umin(n, *n_dev);
     uint32_t begin, end;
     slice_of(n, gridDim.x, blockIdx.x, begin, end);
     if (threadIdx.x == 0) carry = bsum[blockIdx.x];
@@ -292,10 +296,11 @@ __global__ void __launch_bounds__(256) k_tile_scan(const uint32_t* __restrict__ 
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ tiles,
                                               const uint32_t* __restrict__ off, const float4* __restrict__ rec,
                                               const DevCamera* __restrict__ cams, int n, int tile, uint32_t n_items,
-                                              uint64_t pair_cap, uint32_t* __restrict__ pkey,
-                                              uint32_t* __restrict__ pval, uint32_t* __restrict__ overflow) {
+                                              const uint32_t* __restrict__ n_dev, uint64_t pair_cap,
+                                              uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval,
+                                              uint32_t* __restrict__ overflow) {
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n_items) return;
+    if (k >= n_items || k >= *n_dev) return;
     uint32_t item = order[k];
     uint32_t cnt = tiles[item];
     if (cnt == 0) return;
@@ -350,13 +355,18 @@ cudaError_t radix_sort_pairs(gs_ctx* c, uint32_t** keys, uint32_t** vals, const 
     return cudaGetLastError();
 }
 
-cudaError_t scan_tiles(gs_ctx* c, uint32_t n, cudaStream_t s) {
+cudaError_t scan_tiles(gs_ctx* c, uint32_t n_max, const uint32_t* n_dev, cudaStream_t s) {
     // the depth-sorted order is in dval[0] after the even number (4) of depth passes
     const int G = c->sort_blocks;
     c->launches += 3;
-    k_tile_block_sums<<<G, 256, 0, s>>>(c->dval[0], c->tiles_touched, n, c->hist);
+    k_tile_block_sums<<<G, 256, 0, s>>>(c->dval[0], c->tiles_touched, n_max, n_dev, c->hist);
     k_scan_counts<<<1, 1024, 0, s>>>(c->hist, (uint32_t)G, c->dcount);
-    k_tile_scan<<<G, 256, 0, s>>>(c->dval[0], c->tiles_touched, n, c->hist, c->offsets);
+    k_tile_scan<<<G, 256, 0, s>>>(c->dval[0], c->tiles_touched, n_max, n_dev, c->hist, c->offsets);
+    return cudaGetLastError();
+}
+
+cudaError_t scan_blocks(uint32_t* a, uint32_t n, uint32_t* total_dev, cudaStream_t s) {
+    k_scan_counts<<<1, 1024, 0, s>>>(a, n, total_dev);
     return cudaGetLastError();
 }
 
@@ -364,18 +374,18 @@ cudaError_t scan_u32(gs_ctx* c, const uint32_t* in, uint32_t* out, uint32_t n, u
                      cudaStream_t s) {
     const int G = c->sort_blocks;
     c->launches += 3;
-    k_tile_block_sums<<<G, 256, 0, s>>>(nullptr, in, n, c->hist);
+    k_tile_block_sums<<<G, 256, 0, s>>>(nullptr, in, n, nullptr, c->hist);
     k_scan_counts<<<1, 1024, 0, s>>>(c->hist, (uint32_t)G, total_dev);
-    k_tile_scan<<<G, 256, 0, s>>>(nullptr, in, n, c->hist, out);
+    k_tile_scan<<<G, 256, 0, s>>>(nullptr, in, n, nullptr, c->hist, out);
     return cudaGetLastError();
 }
 
-cudaError_t emit_pairs(gs_ctx* c, uint32_t n_items, cudaStream_t s) {
+cudaError_t emit_pairs(gs_ctx* c, uint32_t n_items, const uint32_t* n_dev, cudaStream_t s) {
     if (n_items == 0) return cudaSuccess;
     ++c->launches;
     k_emit<<<(n_items + 255) / 256, 256, 0, s>>>(c->dval[0], c->tiles_touched, c->offsets, c->rec, c->dcam, c->n,
-                                                 c->tile, n_items, (uint64_t)c->pair_cap, c->pkey[0], c->pval[0],
-                                                 c->dcount + 1);
+                                                 c->tile, n_items, n_dev, (uint64_t)c->pair_cap, c->pkey[0],
+                                                 c->pval[0], c->dcount + 1);
     return cudaGetLastError();
 }
 
