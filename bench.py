@@ -279,8 +279,8 @@ def run_ours(args):
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
     from paper_2504_02437_gb300 import build as B
-    if rank == 0 or not os.path.exists(B.LIB):
-        B.build()
+    if rank == 0:
+        B.build()          # one rank compiles (an up-to-date library is left alone); the others wait
     barrier(world)
     from paper_2504_02437_gb300.api import GaussianMap
 
