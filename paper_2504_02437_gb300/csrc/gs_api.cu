@@ -365,6 +365,7 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         }
         ok = ok && dalloc(&c->offsets, V * cap) == cudaSuccess;
         ok = ok && dalloc(&c->ranges, (size_t)c->max_bins) == cudaSuccess;
+        ok = ok && dalloc(&c->work_order, (size_t)c->max_bins) == cudaSuccess;
         ok = ok && dalloc(&c->T_final, V * maxpix) == cudaSuccess;
         ok = ok && dalloc(&c->n_last, V * maxpix) == cudaSuccess;
         ok = ok && dalloc(&c->dLdC, 3 * V * maxpix) == cudaSuccess;
@@ -420,7 +421,7 @@ void gs_destroy(gs_ctx* c) {
     for (auto e : c->tpool) cudaEventDestroy(e);
     void* ptrs[] = {c->params, c->grads, c->adam_m, c->adam_v, c->dens_sum, c->dens_cnt, c->dom_cnt, c->adam_pw, c->dcam, c->rec,
                     c->tiles_touched, c->depth, c->dkey[0], c->dkey[1], c->dval[0], c->dval[1], c->offsets, c->ranges,
-                    c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->vis_blocks, (void*)c->target_slot, c->ssim_maps, c->ssim_part, c->dcount,
+                    c->work_order, c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->vis_blocks, (void*)c->target_slot, c->ssim_maps, c->ssim_part, c->dcount,
                     c->partials, c->fpart,
                     c->own_rgb};
     for (void* p : ptrs) cudaFree(p);

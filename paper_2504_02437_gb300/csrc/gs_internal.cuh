@@ -98,6 +98,7 @@ struct gs_ctx {
     int pair_buf = 0;                       // which of the two buffers holds the sorted pairs
     uint32_t pairs_hint = 0;                // host-side pair count of the last render (grid sizing)
     uint2* ranges = nullptr;                // [max bins] (start, end) per bin
+    uint32_t* work_order = nullptr;         // [max bins] bins by decreasing pair count
     int max_bins = 0;
     float* T_final = nullptr;               // [max_views * H * W]
     uint32_t* n_last = nullptr;             // [max_views * H * W] entries up to the last blended

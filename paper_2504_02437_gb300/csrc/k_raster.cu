@@ -676,14 +676,14 @@ static void fwd_launch(gs_ctx* c, const DevConst& k, float* rgb, int32_t* argmax
         k_raster_fwd<TILE, PPT, true><<<grid, NT, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width, c->height,
                                                           c->hcam[0].tiles_x, tpv, c->n, k, rgb, c->T_final,
                                                           c->n_last, argmax, c->dcount + 6, (uint32_t)c->n_bins,
-                                                          nullptr);
+                                                          c->work_order);
     } else {
         const int grid =
             std::min(resident_grid<1, TILE, PPT>(k_raster_fwd<TILE, PPT, false>, NT, c->num_sms), c->n_bins);
         k_raster_fwd<TILE, PPT, false><<<grid, NT, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width,
                                                            c->height, c->hcam[0].tiles_x, tpv, c->n, k, rgb,
                                                            c->T_final, c->n_last, nullptr, c->dcount + 6,
-                                                           (uint32_t)c->n_bins, nullptr);
+                                                           (uint32_t)c->n_bins, c->work_order);
     }
 }
 
@@ -693,7 +693,7 @@ static void bwd_launch(gs_ctx* c, const DevConst& k, const float* dLdC, cudaStre
     const int grid = std::min(resident_grid<2, TILE, PPT>(k_raster_bwd<TILE, PPT>, NT, c->num_sms), c->n_bins);
     k_raster_bwd<TILE, PPT><<<grid, NT, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width, c->height,
                                                 c->hcam[0].tiles_x, tpv, k, c->T_final, c->n_last, dLdC, c->grad2d,
-                                                c->dcount + 7, (uint32_t)c->n_bins, nullptr);
+                                                c->dcount + 7, (uint32_t)c->n_bins, c->work_order);
 }
 
 template <int TILE, int PPT>
@@ -706,7 +706,7 @@ static void fused_launch(gs_ctx* c, const DevConst& k, const float* target, cons
     k_raster_fused<TILE, PPT><<<grid, NT, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width, c->height,
                                                   c->hcam[0].tiles_x, tpv, k, target, target_slot, scale, rgb,
                                                   c->grad2d, partials,
-                                                  c->dcount + 6, (uint32_t)c->n_bins, nullptr);
+                                                  c->dcount + 6, (uint32_t)c->n_bins, c->work_order);
     *grid_out = grid;
 }
 

@@ -334,6 +334,54 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ pke
     }
 }
 
+// Bucket of a bin in the longest-first work order: 1023 - key, where the key
+// grows with the bin's pair count (steps of 2 pairs below 1,024 pairs, of 16
+// up to 9,200, one bucket above).
+__device__ __forceinline__ uint32_t order_slot(uint2 r) {
+    const uint32_t len = r.y - r.x;
+    const uint32_t key = len < 1024u ? len >> 1 : 512u + min(511u, (len - 1024u) >> 4);
+    return 1023u - key;
+}
+
+// Longest-first order of the bins for the persistent compositing kernels
+// (list scheduling, largest job first): their work queue hands out the tiles
+// with the most pairs first, so a launch does not end on a long tile taken
+// late. One CTA, a counting sort by bucket; bins of one bucket come in any
+// order (the compositing result does not depend on which CTA takes a tile).
+__global__ void __launch_bounds__(1024) k_work_order(const uint2* __restrict__ ranges, uint32_t n_bins,
+                                                      uint32_t* __restrict__ order) {
+    __shared__ uint32_t cnt[1024];
+    __shared__ uint32_t wsum[32];
+    const int t = threadIdx.x, lane = t & 31;
+    cnt[t] = 0;
+    __syncthreads();
+    for (uint32_t b = t; b < n_bins; b += 1024) atomicAdd(&cnt[order_slot(ranges[b])], 1u);
+    __syncthreads();
+    const uint32_t v = cnt[t];
+    uint32_t x = v;   // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[t >> 5] = x;
+    __syncthreads();
+    if (t < 32) {
+        const uint32_t w = wsum[t];
+        uint32_t z = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, z, o);
+            if (lane >= o) z += y;
+        }
+        wsum[t] = z - w;
+    }
+    __syncthreads();
+    cnt[t] = x - v + wsum[t >> 5];
+    __syncthreads();
+    for (uint32_t b = t; b < n_bins; b += 1024) order[atomicAdd(&cnt[order_slot(ranges[b])], 1u)] = b;
+}
+
 }  // namespace
 
 cudaError_t radix_sort_pairs(gs_ctx* c, uint32_t** keys, uint32_t** vals, const uint32_t* n_dev, uint32_t n_max,
@@ -394,6 +442,8 @@ cudaError_t compute_ranges(gs_ctx* c, cudaStream_t s) {
     ++c->launches;
     k_ranges<<<c->num_sms * 8, 256, 0, s>>>(c->pkey[c->pair_buf], c->dcount, (uint64_t)c->pair_cap,
                                             (uint32_t)c->n_bins, c->ranges);
+    ++c->launches;
+    k_work_order<<<1, 1024, 0, s>>>(c->ranges, (uint32_t)c->n_bins, c->work_order);
     return cudaGetLastError();
 }
 
