@@ -16,10 +16,20 @@
 namespace gs {
 namespace {
 
-// records staged in shared memory per batch: 512 for CTAs of 256 threads
-// (fewer barriers per tile; 2 % faster than 256 on the 300k-Gaussian keyframe,
-// 128 was 7 % slower), 256 for smaller CTAs (more CTAs per SM share the memory)
-constexpr int batch_for(int threads) { return threads >= 256 ? 512 : 256; }
+// records staged in shared memory per batch: 512 for CTAs of 128 or 256
+// threads (fewer barriers per tile: on the 300k-Gaussian keyframe 2 % faster
+// than 256 for 256 threads, 3 % for 128; 128 records were 7 % slower), 256 for
+// CTAs of 64 threads (there 512 records limit the SM to 6 CTAs by shared memory
+// and the 8-view window slows by 30 %)
+constexpr int batch_for(int threads) { return threads >= 128 ? 512 : 256; }
+
+// A Gaussian that at most this many lanes of a warp blended gets its 9
+// gradient values added by each of those lanes (two float4 atomics and one
+// scalar) instead of a 12-shuffle warp sum and one 9-lane atomic: fewer issue
+// slots for the warp; past about half a warp the same-address atomics cost more
+// (on the 300k-Gaussian keyframe, 16 x 2 layout: 6 % faster than a threshold of
+// one lane, 24 within noise of 16; every lane, 2 % slower)
+constexpr int kLaneAtomicMax = 16;
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -156,18 +166,16 @@ __device__ __forceinline__ float warp_sum9(const float (&v)[9], int lane, int& i
     return z;
 }
 
-// Shared-memory staging of one batch of raster records, shared by the forward
-// and backward passes of a CTA.
-constexpr int kMaxWarps = 8;  // 256 threads per CTA at most
-
-template <int B>
+// Shared-memory staging of one batch of B raster records for a CTA of NW
+// warps, shared by the forward and backward passes.
+template <int B, int NW>
 struct Stage {
     // index of an entry of a staged batch
     typedef typename std::conditional<B <= 256, uint8_t, uint16_t>::type Idx;
     float4 s0[B], s1[B], s2[B];
     uint32_t sid[B];
     uint32_t mask[B];   // bit w: the record's pixel box meets warp w's pixel block
-    Idx list[kMaxWarps][B];   // per warp: the batch entries it must visit, in order
+    Idx list[NW][B];   // per warp: the batch entries it must visit, in order
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -179,8 +187,8 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 // Compacts the entries k < cnt of the staged batch whose mask has this warp's
 // bit (and, when `limit` is given, lie before it) into the warp's list, in
 // ascending order; returns their number. Called by all 32 lanes of the warp.
-template <int B>
-__device__ __forceinline__ int build_warp_list(Stage<B>& st, int cnt, uint32_t base, uint32_t limit) {
+template <int B, int NW>
+__device__ __forceinline__ int build_warp_list(Stage<B, NW>& st, int cnt, uint32_t base, uint32_t limit) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t wbit = 1u << w, lt = lanemask_lt();
     int nk = 0;
@@ -188,15 +196,15 @@ __device__ __forceinline__ int build_warp_list(Stage<B>& st, int cnt, uint32_t b
         const int k = c0 + lane;
         const bool hit = k < cnt && (st.mask[k] & wbit) && base + (uint32_t)k < limit;
         const uint32_t bal = __ballot_sync(0xFFFFFFFFu, hit);
-        if (hit) st.list[w][nk + __popc(bal & lt)] = (typename Stage<B>::Idx)k;
+        if (hit) st.list[w][nk + __popc(bal & lt)] = (typename Stage<B, NW>::Idx)k;
         nk += __popc(bal);
     }
     __syncwarp();
     return nk;
 }
-template <int B>
-__device__ __forceinline__ Stage<B>& stage() {
-    __shared__ Stage<B> st;
+template <int B, int NW>
+__device__ __forceinline__ Stage<B, NW>& stage() {
+    __shared__ Stage<B, NW> st;
     return st;
 }
 
@@ -260,7 +268,7 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
                                          float (&cb)[PPT], uint32_t (&last)[PPT], uint32_t (&amax)[PPT]) {
     constexpr int NT = Layout<TILE, PPT>::kThreads;
     constexpr int kBatch = batch_for(NT);
-    Stage<kBatch>& st = stage<kBatch>();
+    Stage<kBatch, NT / 32>& st = stage<kBatch, NT / 32>();
     float4* s0 = st.s0;
     float4* s1 = st.s1;
     float4* s2 = st.s2;
@@ -294,7 +302,7 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
         __syncthreads();
         const int cnt = min((uint32_t)kBatch, rg.y - bs);
         const int nk = build_warp_list(st, cnt, 0u, 0xFFFFFFFFu);
-        const typename Stage<kBatch>::Idx* wl = st.list[threadIdx.x >> 5];
+        const typename Stage<kBatch, NT / 32>::Idx* wl = st.list[threadIdx.x >> 5];
         for (int i = 0; i < nk && nlive > 0; ++i) {
             const int k = wl[i];
             const float4 a = s0[k];
@@ -336,9 +344,9 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
 // Adjoint of the compositing for a thread's PPT pixels: walks the tile's list
 // back to front from the block's largest last-blended entry, recovering
 // T_i = T_{i+1} / (1 - alpha_i) from the final T, and accumulates the
-// gradients w.r.t. each Gaussian's screen quantities (warp sum, then one
-// 9-lane atomic per Gaussian and warp; when a single lane blended, that lane
-// adds its 9 values itself with two float4 atomics and one scalar). Each
+// gradients w.r.t. each Gaussian's screen quantities (when at most
+// kLaneAtomicMax lanes blended it, each adds its own 9 values with two float4
+// atomics and one scalar; else a warp sum, then one 9-lane atomic). Each
 // warp visits only the batch entries its compacted list holds, which stop at
 // the warp's largest last-blended entry.
 template <int TILE, int PPT>
@@ -349,7 +357,7 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
                                          float* __restrict__ grad2d) {
     constexpr int NT = Layout<TILE, PPT>::kThreads;
     constexpr int kBatch = batch_for(NT);
-    Stage<kBatch>& st = stage<kBatch>();
+    Stage<kBatch, NT / 32>& st = stage<kBatch, NT / 32>();
     float4* s0 = st.s0;
     float4* s1 = st.s1;
     float4* s2 = st.s2;
@@ -389,7 +397,7 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
         }
         __syncthreads();
         const int nk = build_warp_list(st, (int)(be - bs), bs, warp_end);
-        const typename Stage<kBatch>::Idx* wl = st.list[threadIdx.x >> 5];
+        const typename Stage<kBatch, NT / 32>::Idx* wl = st.list[threadIdx.x >> 5];
         for (int i = nk - 1; i >= 0; --i) {
             const int k = wl[i];
             const uint32_t pos = bs + k;
@@ -439,8 +447,8 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
             }
             const uint32_t who = __ballot_sync(0xFFFFFFFFu, any);
             if (who == 0u) continue;
-            if ((who & (who - 1u)) == 0u) {
-                // a single lane blended this Gaussian: it adds its own values (no warp sum)
+            if (__popc(who) <= kLaneAtomicMax) {
+                // few lanes blended this Gaussian: each adds its own values (no warp sum)
                 if (any) {
                     float* gp = grad2d + (size_t)sid[k] * kGrad2dStride;
                     atomicAdd(reinterpret_cast<float4*>(gp), make_float4(acc[0], acc[1], acc[2], acc[3]));
