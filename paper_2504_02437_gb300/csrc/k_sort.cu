@@ -292,35 +292,81 @@ __global__ void __launch_bounds__(256) k_tile_scan(const uint32_t* __restrict__ 
     }
 }
 
-// One thread per depth-sorted (view, Gaussian): write its pairs (bin, item).
+// Pair emission: item k of the depth order owns pairs off[k] .. off[k] + tiles
+// - 1, one per tile of its pixel box in row-major order (bin, item). Each warp
+// takes 32 consecutive items, scans their tile counts, and writes the warp's
+// pairs (a contiguous run of the output) 32 at a time: lane j writes pair t =
+// t0 + j of the run, owned by the last lane whose exclusive count is <= t, so
+// the stores are coalesced and a large Gaussian's pairs are spread over the
+// warp. An item whose pairs would pass pair_cap is skipped and sets *overflow.
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ tiles,
                                               const uint32_t* __restrict__ off, const float4* __restrict__ rec,
                                               const DevCamera* __restrict__ cams, int n, int tile, uint32_t n_items,
                                               const uint32_t* __restrict__ n_dev, uint64_t pair_cap,
                                               uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval,
                                               uint32_t* __restrict__ overflow) {
-    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n_items || k >= *n_dev) return;
-    uint32_t item = order[k];
-    uint32_t cnt = tiles[item];
-    if (cnt == 0) return;
-    uint64_t o = off[k];
-    if (o + cnt > pair_cap) {
-        atomicMax(overflow, 1u);
-        return;
-    }
-    const DevCamera& cam = cams[item / (uint32_t)n];
-    const float4 f0 = rec[(size_t)item * 3], f1 = rec[(size_t)item * 3 + 1], f2 = rec[(size_t)item * 3 + 2];
-    int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
-    pixel_box(f0.x, f1.w, f0.y, f2.w, f0.z, cam.width, cam.height, x0, x1, y0, y1);
-    int tx0 = x0 / tile, tx1 = x1 / tile, ty0 = y0 / tile, ty1 = y1 / tile;
-    const uint64_t o_end = o + cnt;
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1 && o < o_end; ++tx) {
-            pkey[o] = (uint32_t)(cam.bin_base + ty * cam.tiles_x + tx);
-            pval[o] = item;
-            ++o;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nv = umin(n_items, *n_dev);
+    if (k - (uint32_t)lane >= nv) return;   // the whole warp is past the visible items
+    uint32_t item = 0, cnt = 0, o = 0, bin0 = 0, tiles_x = 0;
+    int tx0 = 0, ty0 = 0, wt = 1;
+    if (k < nv) {
+        item = order[k];
+        cnt = tiles[item];
+        if (cnt != 0) {
+            o = off[k];
+            if ((uint64_t)o + cnt > pair_cap) {
+                atomicMax(overflow, 1u);
+                cnt = 0;
+            } else {
+                const DevCamera& cam = cams[item / (uint32_t)n];
+                const float4 f0 = rec[(size_t)item * 3], f1 = rec[(size_t)item * 3 + 1],
+                             f2 = rec[(size_t)item * 3 + 2];
+                int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
+                pixel_box(f0.x, f1.w, f0.y, f2.w, f0.z, cam.width, cam.height, x0, x1, y0, y1);
+                tx0 = x0 / tile;
+                ty0 = y0 / tile;
+                wt = x1 / tile - tx0 + 1;
+                bin0 = (uint32_t)cam.bin_base;
+                tiles_x = (uint32_t)cam.tiles_x;
+            }
         }
+    }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const uint32_t excl = incl - cnt;
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+        const uint32_t t = t0 + (uint32_t)lane;
+        int src = 0;   // last lane with excl <= t (lanes without pairs share the next lane's excl)
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int cand = src + step;
+            const uint32_t e = __shfl_sync(0xFFFFFFFFu, excl, cand & 31);
+            if (cand < 32 && e <= t) src = cand;
+        }
+        const uint32_t s_excl = __shfl_sync(0xFFFFFFFFu, excl, src);
+        const uint32_t s_o = __shfl_sync(0xFFFFFFFFu, o, src);
+        const uint32_t s_item = __shfl_sync(0xFFFFFFFFu, item, src);
+        const uint32_t s_bin0 = __shfl_sync(0xFFFFFFFFu, bin0, src);
+        const uint32_t s_tx = __shfl_sync(0xFFFFFFFFu, tiles_x, src);
+        const int s_tx0 = __shfl_sync(0xFFFFFFFFu, tx0, src);
+        const int s_ty0 = __shfl_sync(0xFFFFFFFFu, ty0, src);
+        const int s_wt = __shfl_sync(0xFFFFFFFFu, wt, src);
+        if (t < total) {
+            const uint32_t local = t - s_excl;
+            const uint32_t row = local / (uint32_t)s_wt;
+            const uint32_t col = local - row * (uint32_t)s_wt;
+            const uint32_t pos = s_o + local;
+            pkey[pos] = s_bin0 + (uint32_t)(s_ty0 + (int)row) * s_tx + (uint32_t)(s_tx0 + (int)col);
+            pval[pos] = s_item;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ pkey, const uint32_t* __restrict__ P_dev,
