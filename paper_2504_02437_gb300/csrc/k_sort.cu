@@ -152,34 +152,41 @@ __global__ void __launch_bounds__(256) k_digit_scan(uint32_t* __restrict__ hist,
 // kRound elements; warp w of a round owns a contiguous run of 32*kSortItems
 // elements, ranked within the warp by __match_any_sync, across warps by a
 // per-digit prefix over the warps' counts, and across blocks by the scanned
-// histogram.
+// histogram. The ranked round is first regrouped by digit in shared memory,
+// then written out by consecutive threads, so each digit's run of the round
+// leaves in coalesced stores instead of one scattered store per element.
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* __restrict__ n_dev, uint32_t n_max, int shift, int nbits,
     const uint32_t* __restrict__ hist, const uint32_t* __restrict__ dtot) {
-    __shared__ uint32_t run[256];
-    __shared__ uint32_t total[256];
+    __shared__ uint32_t run[256];      // global position of the block's next element of each digit
+    __shared__ uint32_t lstart[256];   // start of each digit's group in the staged round
+    __shared__ uint32_t wsum[kSortWarps];
     __shared__ uint32_t wcnt[kSortWarps][256];
+    __shared__ uint32_t skey[kRound], sval[kRound];
     const int G = gridDim.x, b = blockIdx.x;
     const uint32_t mask = (1u << nbits) - 1u;
     const int ndig = 1 << nbits;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    {
-        // start of each digit = exclusive prefix of the digit totals (one digit per thread)
-        const int d = threadIdx.x;
-        const uint32_t c = d < ndig ? dtot[d] : 0u;
+    // exclusive scan of one value per thread (thread d holds digit d) over the block
+    auto block_scan = [&](uint32_t c) -> uint32_t {
         uint32_t x = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
             if (lane >= o) x += y;
         }
-        if (lane == 31) total[w] = x;
+        if (lane == 31) wsum[w] = x;
         __syncthreads();
         uint32_t pre = 0;
-        for (int k = 0; k < w; ++k) pre += total[k];
-        if (d < ndig) run[d] = pre + x - c + hist[(size_t)d * G + b];
+        for (int k = 0; k < w; ++k) pre += wsum[k];
         __syncthreads();
+        return pre + x - c;
+    };
+    {
+        const int d = threadIdx.x;
+        const uint32_t start = block_scan(d < ndig ? dtot[d] : 0u);
+        if (d < ndig) run[d] = start + hist[(size_t)d * G + b];
     }
     uint32_t n = umin(*n_dev, n_max), begin, end;
     slice_of(n, G, b, begin, end);
@@ -205,29 +212,42 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
             __syncwarp();
         }
         __syncthreads();
-        for (int d = threadIdx.x; d < ndig; d += kSortThreads) {
-            uint32_t s = 0;
+        // per digit: prefix over the warps, the round's count, and its group start in the round
+        uint32_t tot = 0;
+        {
+            const int d = threadIdx.x;
+            if (d < ndig) {
 #pragma unroll
-            for (int ww = 0; ww < kSortWarps; ++ww) {
-                uint32_t c = wcnt[ww][d];
-                wcnt[ww][d] = s;
-                s += c;
+                for (int ww = 0; ww < kSortWarps; ++ww) {
+                    const uint32_t c = wcnt[ww][d];
+                    wcnt[ww][d] = tot;
+                    tot += c;
+                }
             }
-            total[d] = s;
+            const uint32_t ls = block_scan(tot);   // synchronises the block
+            if (d < ndig) lstart[d] = ls;
         }
         __syncthreads();
 #pragma unroll
         for (int it = 0; it < kSortItems; ++it) {
-            uint32_t i = wbase + it * 32 + lane;
+            const uint32_t i = wbase + it * 32 + lane;
             if (i < end) {
-                uint32_t d = (key[it] >> shift) & mask;
-                uint32_t pos = run[d] + wcnt[w][d] + rank[it];
-                kout[pos] = key[it];
-                vout[pos] = val[it];
+                const uint32_t d = (key[it] >> shift) & mask;
+                const uint32_t lp = lstart[d] + wcnt[w][d] + rank[it];
+                skey[lp] = key[it];
+                sval[lp] = val[it];
             }
         }
         __syncthreads();
-        for (int d = threadIdx.x; d < ndig; d += kSortThreads) run[d] += total[d];
+        const uint32_t cnt = umin((uint32_t)kRound, end - rbase);
+        for (uint32_t j = threadIdx.x; j < cnt; j += kSortThreads) {
+            const uint32_t k2 = skey[j], d = (k2 >> shift) & mask;
+            const uint32_t pos = run[d] + (j - lstart[d]);
+            kout[pos] = k2;
+            vout[pos] = sval[j];
+        }
+        __syncthreads();
+        if (threadIdx.x < ndig) run[threadIdx.x] += tot;
         __syncthreads();
     }
 }
