@@ -380,6 +380,7 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
                                                                        cfg->max_views)) == cudaSuccess;
         }
         ok = ok && dalloc(&c->partials, (size_t)c->n_partials + 8) == cudaSuccess;
+        ok = ok && dalloc(&c->reg_part, (cap + 255) / 256 + 1) == cudaSuccess;
         c->n_fpart = 32 * c->num_sms;   // at most 32 resident CTAs per SM
         ok = ok && dalloc(&c->fpart, (size_t)c->n_fpart) == cudaSuccess;
         ok = ok && alloc_pairs(c, pc) == cudaSuccess;
@@ -422,7 +423,7 @@ void gs_destroy(gs_ctx* c) {
     void* ptrs[] = {c->params, c->grads, c->adam_m, c->adam_v, c->dens_sum, c->dens_cnt, c->dom_cnt, c->adam_pw, c->dcam, c->rec,
                     c->tiles_touched, c->depth, c->dkey[0], c->dkey[1], c->dval[0], c->dval[1], c->offsets, c->ranges,
                     c->work_order, c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->vis_blocks, (void*)c->target_slot, c->ssim_maps, c->ssim_part, c->dcount,
-                    c->partials, c->fpart,
+                    c->partials, c->reg_part, c->fpart,
                     c->own_rgb};
     for (void* p : ptrs) cudaFree(p);
     free_pairs(c);

@@ -121,6 +121,7 @@ struct gs_ctx {
     uint32_t visible_hint = 0;              // host copy of dcount[8] from the last synchronising render
     uint32_t* hcount = nullptr;             // pinned host mirror
     float* partials = nullptr;              // reduction partials
+    float* reg_part = nullptr;              // [ceil(cap / 256)] planar-term partials of the last projection
     float* fpart = nullptr;                 // photometric partials of the fused kernel (one per CTA)
     int n_fpart = 0;
     int n_partials = 0;
@@ -193,7 +194,7 @@ cudaError_t launch_count_work(gs_ctx* c, const DevConst& k, unsigned long long* 
 // the screen-space gradients and one photometric partial per CTA (at most max_grid CTAs)
 cudaError_t launch_raster_fused(gs_ctx* c, const DevConst& k, const float* target, const float* const* target_slot,
                                 float* rgb, float* partials, int max_grid, int* grid_out, cudaStream_t s);
-// planar term partials + the final fixed-order sum of photometric and planar partials
+// the fixed-order sum of the photometric partials and the projection's planar-term partials
 cudaError_t launch_loss_tail(gs_ctx* c, const DevConst& k, const float* photo_partials, int n_photo,
                              float* loss_out, cudaStream_t s);
 cudaError_t launch_loss(gs_ctx* c, const DevConst& k, const float* rgb, const float* target, float* loss_out,

@@ -160,13 +160,15 @@ __device__ __forceinline__ bool preprocess_one(const float* __restrict__ P, int 
                                                const DevCamera* __restrict__ cams, const DevConst& kc, int tile,
                                                float4* __restrict__ rec, uint32_t* __restrict__ tiles,
                                                uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval,
-                                               float* __restrict__ depth) {
+                                               float* __restrict__ depth, float& planar) {
     const DevCamera& cam = cams[view];
     size_t item = (size_t)view * n + gid;
     float p[kParamRows];
     load_params(P, cap, gid, p);
     Shape g;
     shape_of(p, g);
+    // the Gaussian's planar term of Eq. 10: max(floor, smallest scale)
+    planar = fmaxf(kc.reg_floor, fminf(g.s[0], fminf(g.s[1], g.s[2])));
     Proj o;
     project_one(p, g, cam, kc.dilation, o);
     // Screen mean and depth in float-float (the covariance stays float32): the
@@ -213,18 +215,34 @@ __device__ __forceinline__ bool preprocess_one(const float* __restrict__ P, int 
 
 // One thread per (view, Gaussian) item; each CTA also writes how many of its 256
 // consecutive items are visible (block_vis[view * gridDim.x + blockIdx.x]), the
-// first step of the order-keeping compaction ahead of the depth sort.
+// first step of the order-keeping compaction ahead of the depth sort, and the
+// CTAs of view 0 the sum of their Gaussians' planar terms times reg_scale
+// (reg_part[blockIdx.x]; the loss adds these partials in index order).
 __global__ void __launch_bounds__(256) k_preprocess(const float* __restrict__ P, int n, int cap,
                                                     const DevCamera* __restrict__ cams, DevConst kc, int tile,
                                                     float4* __restrict__ rec, uint32_t* __restrict__ tiles,
                                                     uint32_t* __restrict__ dkey, uint32_t* __restrict__ dval,
-                                                    float* __restrict__ depth, uint32_t* __restrict__ block_vis) {
+                                                    float* __restrict__ depth, uint32_t* __restrict__ block_vis,
+                                                    float reg_scale, float* __restrict__ reg_part) {
+    __shared__ float wsum[8];
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     const int view = blockIdx.y;
     bool vis = false;
-    if (gid < n) vis = preprocess_one(P, n, cap, gid, view, cams, kc, tile, rec, tiles, dkey, dval, depth);
+    float planar = 0.f;
+    if (gid < n) vis = preprocess_one(P, n, cap, gid, view, cams, kc, tile, rec, tiles, dkey, dval, depth, planar);
     const int cnt = __syncthreads_count(vis);
     if (threadIdx.x == 0) block_vis[(size_t)view * gridDim.x + blockIdx.x] = (uint32_t)cnt;
+    if (view == 0) {   // uniform over the CTA
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) planar += __shfl_xor_sync(0xFFFFFFFFu, planar, o);
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = planar;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+            for (int w = 0; w < 8; ++w) t += wsum[w];
+            reg_part[blockIdx.x] = t * reg_scale;
+        }
+    }
 }
 
 // Order-keeping compaction of the visible items: CTA b (the items of preprocess
@@ -421,7 +439,8 @@ cudaError_t launch_preprocess(gs_ctx* c, int n_views, const DevConst& k, cudaStr
     const uint32_t nblocks = grid.x * grid.y;
     c->launches += 3;
     k_preprocess<<<grid, 256, 0, s>>>(c->params, c->n, c->cap, c->dcam, k, c->tile, c->rec, c->tiles_touched,
-                                       c->dkey[1], c->dval[1], c->depth, c->vis_blocks);
+                                       c->dkey[1], c->dval[1], c->depth, c->vis_blocks,
+                                       k.lambda_reg / (float)c->n, c->reg_part);
     cudaError_t e = scan_blocks(c->vis_blocks, nblocks, c->dcount + 8, s);
     if (e != cudaSuccess) return e;
     k_compact_visible<<<grid, 256, 0, s>>>(c->dkey[1], c->dval[1], c->n, c->vis_blocks, c->dkey[0], c->dval[0]);

@@ -49,52 +49,36 @@ __global__ void __launch_bounds__(kRedThreads) k_l1(const float* __restrict__ rg
     if (threadIdx.x == 0) partials[blockIdx.x] = t * scale;
 }
 
-// Planar term of Eq. 10: partial sums of max(floor, min_k exp(log-scale_k)).
-__global__ void __launch_bounds__(kRedThreads) k_planar(const float* __restrict__ P, int n, int cap, float floor_,
-                                                        float scale, float* __restrict__ partials) {
-    __shared__ float sh[kRedThreads / 32];
-    float acc = 0.f;
-    for (int i = blockIdx.x * kRedThreads + threadIdx.x; i < n; i += gridDim.x * kRedThreads) {
-        float s0 = expf(P[3 * (size_t)cap + i]), s1 = expf(P[4 * (size_t)cap + i]), s2 = expf(P[5 * (size_t)cap + i]);
-        acc += fmaxf(floor_, fminf(s0, fminf(s1, s2)));
-    }
-    float t = block_sum(acc, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = t * scale;
-}
-
-// Fixed-order final reduction: out = {photometric + planar, photometric, planar}.
-__global__ void __launch_bounds__(32) k_loss_final(const float* __restrict__ partials, int n_img, int n_reg,
-                                                   float* __restrict__ out) {
+// Fixed-order final reduction: out = {photometric + planar, photometric,
+// planar} from the photometric partials and the planar-term partials the
+// projection wrote. Thread t adds entries t, t + 256, ... in float64; the warp
+// and CTA trees are fixed, so the result does not vary from run to run.
+__global__ void __launch_bounds__(kRedThreads) k_loss_final(const float* __restrict__ photo, int n_photo,
+                                                            const float* __restrict__ reg, int n_reg,
+                                                            float* __restrict__ out) {
+    __shared__ double sa[kRedThreads / 32], sb[kRedThreads / 32];
     double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < n_img; i += 32) a += partials[i];
-    for (int i = threadIdx.x; i < n_reg; i += 32) b += partials[n_img + i];
+    for (int i = threadIdx.x; i < n_photo; i += kRedThreads) a += photo[i];
+    for (int i = threadIdx.x; i < n_reg; i += kRedThreads) b += reg[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
         b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
     }
-    if (threadIdx.x == 0) {
-        out[0] = (float)(a + b);
-        out[1] = (float)a;
-        out[2] = (float)b;
+    if ((threadIdx.x & 31) == 0) {
+        sa[threadIdx.x >> 5] = a;
+        sb[threadIdx.x >> 5] = b;
     }
-}
-
-// Fixed-order final reduction from two partial arrays.
-__global__ void __launch_bounds__(32) k_loss_final2(const float* __restrict__ photo, int n_photo,
-                                                    const float* __restrict__ reg, int n_reg, float* __restrict__ out) {
-    double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < n_photo; i += 32) a += photo[i];
-    for (int i = threadIdx.x; i < n_reg; i += 32) b += reg[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
-        b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
-    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        out[0] = (float)(a + b);
-        out[1] = (float)a;
-        out[2] = (float)b;
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < kRedThreads / 32; ++w) {
+            ta += sa[w];
+            tb += sb[w];
+        }
+        out[0] = (float)(ta + tb);
+        out[1] = (float)ta;
+        out[2] = (float)tb;
     }
 }
 
@@ -140,28 +124,26 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, const float
 
 }  // namespace
 
+// Planar-term partials of the last projection (view 0's CTAs; none without Gaussians).
+static int reg_partials(const gs_ctx* c) { return (c->n + 255) / 256; }
+
 cudaError_t launch_loss(gs_ctx* c, const DevConst& k, const float* rgb, const float* target, float* loss_out,
                         cudaStream_t s) {
     const size_t HW = (size_t)c->width * c->height;
     const size_t total = (size_t)c->n_views * 3 * HW;
-    const int nb_img = c->n_partials / 2, nb_reg = c->n_partials / 2;
+    const int nb_img = c->n_partials / 2;
     const float scale = k.lambda_color / (float)(3 * HW);
-    c->launches += 3;
+    c->launches += 2;
     k_l1<<<nb_img, kRedThreads, 0, s>>>(rgb, target, total, scale, c->dLdC, c->partials);
-    k_planar<<<nb_reg, kRedThreads, 0, s>>>(c->params, c->n, c->cap, k.reg_floor,
-                                            c->n > 0 ? k.lambda_reg / (float)c->n : 0.f, c->partials + nb_img);
-    k_loss_final<<<1, 32, 0, s>>>(c->partials, nb_img, nb_reg, loss_out);
+    k_loss_final<<<1, kRedThreads, 0, s>>>(c->partials, nb_img, c->reg_part, reg_partials(c), loss_out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_loss_tail(gs_ctx* c, const DevConst& k, const float* photo_partials, int n_photo,
                              float* loss_out, cudaStream_t s) {
-    const int nb_reg = c->n_partials / 2;
-    float* reg_part = c->partials + c->n_partials / 2;
-    c->launches += 2;
-    k_planar<<<nb_reg, kRedThreads, 0, s>>>(c->params, c->n, c->cap, k.reg_floor,
-                                            c->n > 0 ? k.lambda_reg / (float)c->n : 0.f, reg_part);
-    k_loss_final2<<<1, 32, 0, s>>>(photo_partials, n_photo, reg_part, nb_reg, loss_out);
+    (void)k;
+    ++c->launches;
+    k_loss_final<<<1, kRedThreads, 0, s>>>(photo_partials, n_photo, c->reg_part, reg_partials(c), loss_out);
     return cudaGetLastError();
 }
 
