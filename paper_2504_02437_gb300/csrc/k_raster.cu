@@ -431,11 +431,14 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
                     p2v[p] = power2_split(qxdx, qydx, q.z, dx, dy);
                     hit[p] = pos < my_end[p] && fabsf(dy) <= a.w && p2v[p] >= c.w;
                 }
+                float Gv[PPT];   // all pixels' ex2 back to back (the MUFU pipe has room)
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) Gv[p] = ex2_approx(p2v[p]);
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
                     if (!hit[p]) continue;
                     const float dy = fy[p] - a.y;
-                    const float G = ex2_approx(p2v[p]);
+                    const float G = Gv[p];
                     const float oG = __fmul_rn(q.w, G);
                     const float alpha = fminf(kc.alpha_max, oG);
                     any = true;
