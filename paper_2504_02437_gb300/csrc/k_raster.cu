@@ -303,8 +303,10 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
         const int cnt = min((uint32_t)kBatch, rg.y - bs);
         const int nk = build_warp_list(st, cnt, 0u, 0xFFFFFFFFu);
         const typename Stage<kBatch, NT / 32>::Idx* wl = st.list[threadIdx.x >> 5];
+        int knext = nk > 0 ? (int)wl[0] : 0;   // the next entry's index is loaded one visit ahead
         for (int i = 0; i < nk && nlive > 0; ++i) {
-            const int k = wl[i];
+            const int k = knext;
+            if (i + 1 < nk) knext = wl[i + 1];
             const float4 a = s0[k];
             const float dx = g.fx - a.x;
             if (fabsf(dx) > a.z) continue;
