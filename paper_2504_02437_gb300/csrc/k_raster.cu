@@ -410,8 +410,10 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
         __syncthreads();
         const int nk = build_warp_list(st, (int)(be - bs), bs, warp_end);
         const typename Stage<kBatch, NT / 32>::Idx* wl = st.list[threadIdx.x >> 5];
+        int knext = nk > 0 ? (int)wl[nk - 1] : 0;   // as in the forward: one visit ahead
         for (int i = nk - 1; i >= 0; --i) {
-            const int k = wl[i];
+            const int k = knext;
+            if (i > 0) knext = wl[i - 1];
             const uint32_t pos = bs + k;
             const float4 a = s0[k];
             const float dx = g.fx - a.x;
