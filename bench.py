@@ -47,7 +47,7 @@ FP32_LANES_PER_SM = 128
 # workload, with the kernel source's sha256 and layout at capture time (the figure is reported
 # only while both still match): profiles/raster_fused_replica_1200x680_300k.md
 NCU_TRAFFIC = {"raster_fused": {"bytes": 35.95e6, "source": "paper_2504_02437_gb300/csrc/k_raster.cu",
-                                "sha256": "90a9dd07c712a66d99c530f77d1128bdc41449490e617fcacecef148602bf9fb",
+                                "sha256": "b06af8cea590eb21f73e1094f82712851e86c67d3fb512ad1dcc17c4afcc2fb8",
                                 "tile": 16, "ppt": 2}}
 
 
