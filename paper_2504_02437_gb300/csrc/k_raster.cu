@@ -27,9 +27,9 @@ constexpr int batch_for(int threads) { return threads >= 128 ? 512 : 256; }
 // gradient values added by each of those lanes (two float4 atomics and one
 // scalar) instead of a 12-shuffle warp sum and one 9-lane atomic: fewer issue
 // slots for the warp; past about half a warp the same-address atomics cost more
-// (on the 300k-Gaussian keyframe, 16 x 2 layout: 6 % faster than a threshold of
-// one lane, 24 within noise of 16; every lane, 2 % slower)
-constexpr int kLaneAtomicMax = 16;
+// (on the 300k-Gaussian keyframe, 16 x 2 layout: 7 % faster than a threshold of
+// one lane, 24 about 1 % faster than 16 and 12; every lane, 2 % slower)
+constexpr int kLaneAtomicMax = 24;
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -418,7 +418,6 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
             const float4 a = s0[k];
             const float dx = g.fx - a.x;
             const bool col = fabsf(dx) <= a.z && pos < thread_end;
-            if (!__any_sync(0xFFFFFFFFu, col)) continue;
             float acc[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) acc[i] = 0.f;
