@@ -47,6 +47,8 @@ extern "C" {
 #define GS_ERR_TIMEOUT (-5)    /* a bounded device-side wait gave up                    */
 #define GS_ERR_NONFINITE (-6)  /* a non-finite loss or parameter was detected          */
 #define GS_ERR_STATE (-7)      /* call out of order (e.g. backward before render)       */
+#define GS_ERR_IO (-8)         /* a file could not be read or written, or is not a
+                                  valid checkpoint of this format and version          */
 
 #define GS_MAX_VIEWS 16
 
@@ -275,6 +277,40 @@ GS_API int gs_timing_phases(gs_ctx* ctx, uint32_t mask);
  * milliseconds (ms_host[GS_N_PHASES]) and the number of recorded intervals
  * (counts_host[GS_N_PHASES], may be NULL); clears the records. */
 GS_API int gs_timing_read(gs_ctx* ctx, float* ms_host, int32_t* counts_host);
+
+/* Checkpoint and resume of the map being optimised (Section 3.2); the paper
+ * has no counterpart, the format is this library's own. A checkpoint holds
+ * everything a later mapping iteration reads besides the cameras and
+ * images: the n Gaussians' parameters, their Adam first and second moments,
+ * the Adam step counters and running powers of beta1, beta2 (so the bias
+ * correction continues where it stopped), and the densification statistics
+ * (summed screen-gradient norms, their counts, the dominance counts of
+ * gs_count_dominant). The splitting noise is a counter-based function of the
+ * seed in gs_config and needs no state.
+ *
+ * File format, little-endian, version 1: a 64-byte header
+ *   char magic[8] = "GSMAPCK1"; uint32 version = 1; uint32 rows = 14;
+ *   uint32 n; uint32 adam_steps_device; int32 adam_steps_host; uint32 0;
+ *   float64 beta_powers[2]; uint64 payload_bytes; uint64 fnv1a64(payload)
+ * followed by the payload (payload_bytes = 180 n): float32 params[14][n],
+ * float32 m[14][n], float32 v[14][n], float32 grad_norm_sum[n],
+ * float32 grad_norm_count[n], uint32 dominance[n]. */
+/* Synchronises `stream`, then writes the context's map state to `path`
+ * (created or replaced). Errors: GS_ERR_ARG (NULL argument), GS_ERR_IO (the
+ * file cannot be written), GS_ERR_CUDA. The context is not changed. */
+GS_API int gs_save(gs_ctx* ctx, const char* path, void* stream);
+/* Reads and checks the whole file at `path` (magic, version, sizes, checksum)
+ * before it touches the context, then replaces the context's map state with
+ * it, synchronising `stream`. Per-render state is dropped: a gs_render or
+ * gs_iterate comes next. Errors: GS_ERR_ARG (NULL argument), GS_ERR_IO
+ * (missing, truncated, corrupt or other-format file), GS_ERR_CAPACITY (more
+ * Gaussians than the context holds); on any of these the context is
+ * unchanged. GS_ERR_CUDA. */
+GS_API int gs_load(gs_ctx* ctx, const char* path, void* stream);
+/* Checks the checkpoint at `path` as gs_load does, without a context or a
+ * GPU, and writes its number of Gaussians and format version (either pointer
+ * may be NULL). Returns GS_OK or GS_ERR_ARG (NULL path) or GS_ERR_IO. */
+GS_API int gs_checkpoint_info(const char* path, int* n_host, int* version_host);
 
 /* Stable LSD radix sort of n (key, value) pairs by the low `bits` bits of the
  * key, for callers that cannot allocate device memory: those that run while

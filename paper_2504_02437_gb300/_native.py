@@ -18,11 +18,12 @@ GS_ERR_CUDA = -4
 GS_ERR_TIMEOUT = -5
 GS_ERR_NONFINITE = -6
 GS_ERR_STATE = -7
+GS_ERR_IO = -8
 GS_MAX_VIEWS = 16
 
 ERR_NAMES = {GS_ERR_ARG: "GS_ERR_ARG", GS_ERR_OOM: "GS_ERR_OOM", GS_ERR_CAPACITY: "GS_ERR_CAPACITY",
              GS_ERR_CUDA: "GS_ERR_CUDA", GS_ERR_TIMEOUT: "GS_ERR_TIMEOUT", GS_ERR_NONFINITE: "GS_ERR_NONFINITE",
-             GS_ERR_STATE: "GS_ERR_STATE"}
+             GS_ERR_STATE: "GS_ERR_STATE", GS_ERR_IO: "GS_ERR_IO"}
 
 
 class gs_camera(C.Structure):
@@ -73,6 +74,9 @@ SIGNATURES = {
     "gs_debug_work": (_I, [_P, _P]),
     "gs_launch_count": (C.c_int64, [_P]),
     "gs_sort_pairs_static": (_I, [_P, _P, _P, _P, C.c_int64, _I, _P]),
+    "gs_save": (_I, [_P, C.c_char_p, _P]),
+    "gs_load": (_I, [_P, C.c_char_p, _P]),
+    "gs_checkpoint_info": (_I, [C.c_char_p, C.POINTER(_I), C.POINTER(_I)]),
     "gs_mlp_create": (_I, [_I, C.c_uint64, C.POINTER(_P)]),
     "gs_mlp_destroy": (None, [_P]),
     "gs_mlp_num_params": (_I, []),

@@ -7,6 +7,7 @@ context; ``rasterize`` wraps render/backward as a ``torch.autograd.Function``.
 from __future__ import annotations
 
 import ctypes as C
+import os
 from typing import Optional, Sequence
 
 import numpy as np
@@ -211,6 +212,17 @@ class GaussianMap:
         self._check(self.lib.gs_densify(self.ctx, _ptr(nz), C.byref(n), _stream()))
         return n.value
 
+    # ---- checkpoint / resume
+    def save(self, path: str) -> None:
+        """Write the map state (parameters, Adam moments and step state, densification
+        statistics) to ``path``; waits for the current stream's work first."""
+        self._check(self.lib.gs_save(self.ctx, os.fsencode(path), _stream()))
+
+    def load(self, path: str) -> None:
+        """Replace the map state with the checkpoint at ``path`` (checked in full first)."""
+        self._check(self.lib.gs_load(self.ctx, os.fsencode(path), _stream()))
+        self._last_views = 0
+
     # ---- timing
     def timing(self, enable: bool = True, phases=None):
         """Start (discarding earlier records) or stop per-phase device timing; ``phases`` (names of
@@ -255,6 +267,15 @@ class GaussianMap:
         out = np.empty((self._last_views, 9, self.n), np.float32)
         self._check(self.lib.gs_debug_grad2d(self.ctx, out.ctypes.data_as(C.c_void_p)))
         return out
+
+
+def checkpoint_info(path: str) -> dict:
+    """Number of Gaussians and format version of a checkpoint, after the same checks as a
+    load; raises if the file is missing or not a valid checkpoint. Needs no GPU."""
+    lib = N.load()
+    n, ver = C.c_int(), C.c_int()
+    N.check(lib.gs_checkpoint_info(os.fsencode(path), C.byref(n), C.byref(ver)), None)
+    return {"n": n.value, "version": ver.value}
 
 
 class MLP:

@@ -1165,3 +1165,143 @@ int gs_densify(gs_ctx* c, const float* normals, int* n_split_out, void* stream) 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Checkpoint and resume of the map state (format in gs.h).
+
+namespace {
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, rows, n, adam_steps_device;
+    int32_t adam_steps_host;
+    uint32_t reserved;
+    double beta_powers[2];
+    uint64_t payload_bytes, checksum;
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header layout");
+constexpr char kCkptMagic[8] = {'G', 'S', 'M', 'A', 'P', 'C', 'K', '1'};
+constexpr uint32_t kCkptVersion = 1;
+constexpr uint64_t kCkptBytesPerGaussian = 4ull * (3 * kParamRows + 3);
+
+// FNV-1a, 64-bit (Fowler, Noll, Vo)
+uint64_t fnv1a64(const unsigned char* p, size_t n) {
+    uint64_t h = 0xcbf29ce484222325ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+// Reads and checks a whole checkpoint; on success `payload` holds its arrays.
+// Returns nullptr or the reason it is not a valid checkpoint.
+const char* read_checkpoint(const char* path, CkptHeader& h, std::vector<unsigned char>& payload) {
+    FILE* f = fopen(path, "rb");
+    if (!f) return "cannot open the checkpoint file";
+    const char* why = nullptr;
+    if (fread(&h, sizeof(h), 1, f) != 1) why = "checkpoint shorter than its header";
+    else if (memcmp(h.magic, kCkptMagic, sizeof(kCkptMagic)) != 0) why = "not a checkpoint of this library";
+    else if (h.version != kCkptVersion) why = "unsupported checkpoint version";
+    else if (h.rows != (uint32_t)kParamRows) why = "checkpoint parameter rows differ";
+    else if (h.payload_bytes != kCkptBytesPerGaussian * h.n) why = "checkpoint payload size does not match n";
+    if (!why) {
+        payload.resize((size_t)h.payload_bytes);
+        if (h.payload_bytes && fread(payload.data(), 1, payload.size(), f) != payload.size())
+            why = "checkpoint payload truncated";
+        else if (fgetc(f) != EOF) why = "trailing bytes after the checkpoint payload";
+        else if (fnv1a64(payload.data(), payload.size()) != h.checksum) why = "checkpoint checksum mismatch";
+    }
+    fclose(f);
+    return why;
+}
+
+}  // namespace
+
+int gs_checkpoint_info(const char* path, int* n, int* version) {
+    if (!path) return GS_ERR_ARG;
+    CkptHeader h;
+    std::vector<unsigned char> payload;
+    if (read_checkpoint(path, h, payload)) return GS_ERR_IO;
+    if (n) *n = (int)h.n;
+    if (version) *version = (int)h.version;
+    return GS_OK;
+}
+
+int gs_save(gs_ctx* c, const char* path, void* stream) {
+    if (!c) return GS_ERR_ARG;
+    if (!path) return fail(c, GS_ERR_ARG, "path is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(s));
+    const size_t n = (size_t)c->n;
+    CkptHeader h = {};
+    memcpy(h.magic, kCkptMagic, sizeof(kCkptMagic));
+    h.version = kCkptVersion;
+    h.rows = kParamRows;
+    h.n = (uint32_t)n;
+    h.adam_steps_host = c->adam_t;
+    h.payload_bytes = kCkptBytesPerGaussian * n;
+    std::vector<unsigned char> payload((size_t)h.payload_bytes);
+    float* rows = reinterpret_cast<float*>(payload.data());
+    const float* rows_src[3] = {c->params, c->adam_m, c->adam_v};
+    for (int a = 0; a < 3; ++a)
+        if (n)
+            CK(cudaMemcpy2D(rows + (size_t)a * kParamRows * n, sizeof(float) * n, rows_src[a], sizeof(float) * c->cap,
+                            sizeof(float) * n, kParamRows, cudaMemcpyDeviceToHost));
+    float* tail = rows + (size_t)3 * kParamRows * n;
+    if (n) {
+        CK(cudaMemcpy(tail, c->dens_sum, sizeof(float) * n, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(tail + n, c->dens_cnt, sizeof(float) * n, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(tail + 2 * n, c->dom_cnt, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+    }
+    CK(cudaMemcpy(h.beta_powers, c->adam_pw, sizeof(double) * 2, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&h.adam_steps_device, c->dcount + 4, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    h.checksum = fnv1a64(payload.data(), payload.size());
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(c, GS_ERR_IO, "cannot create the checkpoint file");
+    bool ok = fwrite(&h, sizeof(h), 1, f) == 1 &&
+              (payload.empty() || fwrite(payload.data(), 1, payload.size(), f) == payload.size());
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) return fail(c, GS_ERR_IO, "writing the checkpoint file failed");
+    return GS_OK;
+}
+
+int gs_load(gs_ctx* c, const char* path, void* stream) {
+    if (!c) return GS_ERR_ARG;
+    if (!path) return fail(c, GS_ERR_ARG, "path is NULL");
+    CkptHeader h;
+    std::vector<unsigned char> payload;
+    if (const char* why = read_checkpoint(path, h, payload)) return fail(c, GS_ERR_IO, why);
+    if (h.n > (uint32_t)c->cap) return fail(c, GS_ERR_CAPACITY, "the checkpoint holds more Gaussians than the capacity");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(s));
+    const size_t n = h.n;
+    const float* rows = reinterpret_cast<const float*>(payload.data());
+    float* rows_dst[3] = {c->params, c->adam_m, c->adam_v};
+    CK(cudaMemsetAsync(c->adam_m, 0, sizeof(float) * kParamRows * c->cap, s));
+    CK(cudaMemsetAsync(c->adam_v, 0, sizeof(float) * kParamRows * c->cap, s));
+    CK(cudaMemsetAsync(c->dens_sum, 0, sizeof(float) * c->cap, s));
+    CK(cudaMemsetAsync(c->dens_cnt, 0, sizeof(float) * c->cap, s));
+    CK(cudaMemsetAsync(c->dom_cnt, 0, sizeof(uint32_t) * c->cap, s));
+    CK(cudaStreamSynchronize(s));
+    for (int a = 0; a < 3; ++a)
+        if (n)
+            CK(cudaMemcpy2D(rows_dst[a], sizeof(float) * c->cap, rows + (size_t)a * kParamRows * n, sizeof(float) * n,
+                            sizeof(float) * n, kParamRows, cudaMemcpyHostToDevice));
+    const float* tail = rows + (size_t)3 * kParamRows * n;
+    if (n) {
+        CK(cudaMemcpy(c->dens_sum, tail, sizeof(float) * n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->dens_cnt, tail + n, sizeof(float) * n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->dom_cnt, tail + 2 * n, sizeof(uint32_t) * n, cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(c->adam_pw, h.beta_powers, sizeof(double) * 2, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->dcount + 4, &h.adam_steps_device, sizeof(uint32_t), cudaMemcpyHostToDevice));
+    c->n = (int)n;
+    c->adam_t = h.adam_steps_host;
+    c->n_views = 0;
+    c->loss_ready = c->backward_ready = false;
+    drop_graph(c);
+    return GS_OK;
+}
