@@ -99,6 +99,13 @@ typedef struct gs_config {
     int32_t max_width, max_height; /* largest image of any view                       */
     int64_t pair_capacity; /* (view, tile, Gaussian) pairs per render; 0 = 8 x capacity x max_views */
     uint64_t seed;       /* counter-based generator seed (split samples)              */
+    int32_t deterministic; /* != 0: bitwise-repeatable results (0). No floating-point
+                            atomics: the compositing adjoint writes each (view, tile,
+                            Gaussian) pair's screen gradient into its own slot and a
+                            per-Gaussian pass adds the slots in a fixed order; the
+                            photometric loss is summed per tile. Uses 8-px tiles with 2
+                            pixels per thread (one warp per tile) whatever tile_size and
+                            pixels_per_thread say; slower than the default mode      */
 } gs_config;
 
 /* Fill *cfg with the defaults listed above (capacity 1<<20, 8 views, 1280x720). */

@@ -40,7 +40,8 @@ class gs_config(C.Structure):
                 ("split_factor", C.c_float), ("insert_opacity", C.c_float), ("insert_tau", C.c_float),
                 ("clarity_sigma", C.c_float), ("tile_size", C.c_int32), ("pixels_per_thread", C.c_int32),
                 ("capacity", C.c_int32), ("max_views", C.c_int32), ("max_width", C.c_int32),
-                ("max_height", C.c_int32), ("pair_capacity", C.c_int64), ("seed", C.c_uint64)]
+                ("max_height", C.c_int32), ("pair_capacity", C.c_int64), ("seed", C.c_uint64),
+                ("deterministic", C.c_int32)]
 
 
 _P = C.c_void_p

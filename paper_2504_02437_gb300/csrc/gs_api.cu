@@ -110,6 +110,10 @@ void free_pairs(gs_ctx* c) {
         cudaFree(c->pval[i]);
         c->pkey[i] = c->pval[i] = nullptr;
     }
+    cudaFree(c->emit_item);
+    cudaFree(c->pairgrad);
+    c->emit_item = nullptr;
+    c->pairgrad = nullptr;
 }
 
 cudaError_t alloc_pairs(gs_ctx* c, int64_t cap) {
@@ -119,6 +123,10 @@ cudaError_t alloc_pairs(gs_ctx* c, int64_t cap) {
     for (int i = 0; i < 2; ++i) {
         if ((e = dalloc(&c->pkey[i], (size_t)cap)) != cudaSuccess) return e;
         if ((e = dalloc(&c->pval[i], (size_t)cap)) != cudaSuccess) return e;
+    }
+    if (c->cfg.deterministic) {
+        if ((e = dalloc(&c->emit_item, (size_t)cap)) != cudaSuccess) return e;
+        if ((e = dalloc(&c->pairgrad, (size_t)cap * kPairGradStride)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -143,6 +151,11 @@ const gs_ctx::Tuned* find_tuned(const gs_ctx* c, int w, int h, int views) {
 // Tile size and pixels per thread of a render: the autotuner's candidate while
 // it times one, else the configured values, else the tuned choice, else 16 / 1.
 void pick_layout(gs_ctx* c, int w, int h, int views, int& tile, int& ppt) {
+    if (c->cfg.deterministic) {   // one warp per tile: no ordering question inside a CTA
+        tile = 8;
+        ppt = 2;
+        return;
+    }
     if (c->force_tile) {
         tile = c->force_tile;
         ppt = c->force_ppt;
@@ -317,6 +330,7 @@ void gs_default_config(gs_config* f) {
     f->max_height = 720;
     f->pair_capacity = 0;
     f->seed = 0x5eedULL;
+    f->deterministic = 0;
 }
 
 int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
@@ -381,6 +395,7 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         }
         ok = ok && dalloc(&c->partials, (size_t)c->n_partials + 8) == cudaSuccess;
         ok = ok && dalloc(&c->reg_part, (cap + 255) / 256 + 1) == cudaSuccess;
+        if (cfg->deterministic) ok = ok && dalloc(&c->tile_part, (size_t)c->max_bins) == cudaSuccess;
         c->n_fpart = 32 * c->num_sms;   // at most 32 resident CTAs per SM
         ok = ok && dalloc(&c->fpart, (size_t)c->n_fpart) == cudaSuccess;
         ok = ok && alloc_pairs(c, pc) == cudaSuccess;
@@ -423,7 +438,7 @@ void gs_destroy(gs_ctx* c) {
     void* ptrs[] = {c->params, c->grads, c->adam_m, c->adam_v, c->dens_sum, c->dens_cnt, c->dom_cnt, c->adam_pw, c->dcam, c->rec,
                     c->tiles_touched, c->depth, c->dkey[0], c->dkey[1], c->dval[0], c->dval[1], c->offsets, c->ranges,
                     c->work_order, c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->vis_blocks, (void*)c->target_slot, c->ssim_maps, c->ssim_part, c->dcount,
-                    c->partials, c->reg_part, c->fpart,
+                    c->partials, c->reg_part, c->tile_part, c->fpart,
                     c->own_rgb};
     for (void* p : ptrs) cudaFree(p);
     free_pairs(c);
@@ -558,6 +573,7 @@ int gs_backward(gs_ctx* c, const float* dL_drgb, void* stream) {
     {
         Phase ph(c, GS_PHASE_RASTER_BWD, s);
         CK(launch_raster_backward(c, k, dL_drgb ? dL_drgb : c->dLdC, s));
+        CK(reduce_pair_grads(c, s));   // deterministic mode only
     }
     Phase ph(c, GS_PHASE_PROJECT_BWD, s);
     CK(launch_preprocess_backward(c, k, dL_drgb == nullptr, s));
@@ -652,7 +668,8 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
         rgb = c->own_rgb;
     }
     float* loss_out = loss_dev ? loss_dev : c->partials + c->n_partials;
-    if (c->cfg.tile_size == 0 && c->n > 0 && !find_tuned(c, cams[0].width, cams[0].height, n_views)) {
+    if (c->cfg.tile_size == 0 && !c->cfg.deterministic && c->n > 0 &&
+        !find_tuned(c, cams[0].width, cams[0].height, n_views)) {
         if (n_views < 1 || n_views > c->cfg.max_views) return fail(c, GS_ERR_ARG, "bad views");
         drop_graph(c);
         int code = autotune(c, cams, n_views, target, rgb, s);
@@ -773,12 +790,17 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
             }
             if (cc == GS_OK) {
                 Phase ph(c, GS_PHASE_LOSS, cs);
-                if (launch_loss_tail(c, k, c->fpart, fgrid, loss_out, cs) != cudaSuccess) cc = GS_ERR_CUDA;
+                // the deterministic mode sums the per-tile partials, the default the per-CTA ones
+                const bool det = c->tile_part != nullptr;
+                if (launch_loss_tail(c, k, det ? c->tile_part : c->fpart, det ? c->n_bins : fgrid, loss_out, cs) !=
+                    cudaSuccess)
+                    cc = GS_ERR_CUDA;
             }
         }
         if (cc == GS_OK) {
             Phase ph(c, GS_PHASE_PROJECT_BWD, cs);
-            if (launch_preprocess_backward(c, k, true, cs) != cudaSuccess) cc = GS_ERR_CUDA;
+            if (reduce_pair_grads(c, cs) != cudaSuccess || launch_preprocess_backward(c, k, true, cs) != cudaSuccess)
+                cc = GS_ERR_CUDA;
         }
         if (cc == GS_OK) {
             Phase ph(c, GS_PHASE_ADAM, cs);
@@ -927,7 +949,15 @@ int gs_debug_pairs(gs_ctx* c, uint32_t* bins, uint32_t* vals, int64_t max, int64
     *count = P;
     int64_t m = std::min<int64_t>(P, max);
     if (m > 0 && bins) CK(cudaMemcpy(bins, c->pkey[c->pair_buf], sizeof(uint32_t) * m, cudaMemcpyDeviceToHost));
-    if (m > 0 && vals) CK(cudaMemcpy(vals, c->pval[c->pair_buf], sizeof(uint32_t) * m, cudaMemcpyDeviceToHost));
+    if (m > 0 && vals) {
+        CK(cudaMemcpy(vals, c->pval[c->pair_buf], sizeof(uint32_t) * m, cudaMemcpyDeviceToHost));
+        if (c->emit_item) {   // deterministic mode: the sorted values are emission indices
+            std::vector<uint32_t> items((size_t)std::min<int64_t>(P, c->pair_cap));
+            if (!items.empty())
+                CK(cudaMemcpy(items.data(), c->emit_item, sizeof(uint32_t) * items.size(), cudaMemcpyDeviceToHost));
+            for (int64_t i = 0; i < m; ++i) vals[i] = vals[i] < items.size() ? items[vals[i]] : 0xFFFFFFFFu;
+        }
+    }
     return GS_OK;
 }
 

@@ -14,6 +14,7 @@ namespace gs {
 
 constexpr int kParamRows = 14;
 constexpr int kGrad2dStride = 12;   // floats per (view, Gaussian) screen-gradient record
+constexpr int kPairGradStride = 9;  // floats per pair slot of the deterministic mode
 constexpr int kRecFloat4 = 3;       // float4 per (view, Gaussian) raster record
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
@@ -98,6 +99,11 @@ struct gs_ctx {
     int pair_buf = 0;                       // which of the two buffers holds the sorted pairs
     uint32_t pairs_hint = 0;                // host-side pair count of the last render (grid sizing)
     uint2* ranges = nullptr;                // [max bins] (start, end) per bin
+    // deterministic mode only: the pairs' sort values are emission indices e; emit_item[e] is
+    // the pair's (view, Gaussian) item and pairgrad[9 e ..] its screen-gradient slot
+    uint32_t* emit_item = nullptr;          // [pair capacity]
+    float* pairgrad = nullptr;              // [pair capacity * 9]
+    float* tile_part = nullptr;             // [max bins] photometric loss per (view, tile)
     uint32_t* work_order = nullptr;         // [max bins] bins by decreasing pair count
     int max_bins = 0;
     float* T_final = nullptr;               // [max_views * H * W]
@@ -187,6 +193,8 @@ cudaError_t emit_pairs(gs_ctx* c, uint32_t n_items, const uint32_t* n_dev, cudaS
 // exclusive scan of n u32 values (in may equal out); the total goes to *total_dev
 cudaError_t scan_u32(gs_ctx* c, const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* total_dev, cudaStream_t s);
 cudaError_t compute_ranges(gs_ctx* c, cudaStream_t s);
+// deterministic mode: per-item fixed-order sum of the pair gradient slots into grad2d
+cudaError_t reduce_pair_grads(gs_ctx* c, cudaStream_t s);
 cudaError_t launch_raster_forward(gs_ctx* c, const DevConst& k, float* rgb, int32_t* argmax, cudaStream_t s);
 cudaError_t launch_raster_backward(gs_ctx* c, const DevConst& k, const float* dLdC, cudaStream_t s);
 cudaError_t launch_count_work(gs_ctx* c, const DevConst& k, unsigned long long* out, cudaStream_t s);

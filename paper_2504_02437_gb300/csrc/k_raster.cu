@@ -261,10 +261,10 @@ __device__ __forceinline__ uint32_t warp_mask(const TileGeom<TILE, PPT>& g, cons
 // Forward compositing (Eq. 3) of a thread's PPT pixels over the tile's sorted
 // list. Returns final T, the colour, and per pixel the number of list entries
 // up to and including the last blended Gaussian; optionally the Eq. 8 argmax.
-template <int TILE, int PPT, bool ARGMAX>
+template <int TILE, int PPT, bool ARGMAX, bool DET>
 __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const bool (&inside)[PPT],
-                                         const uint32_t* __restrict__ pval, const float4* __restrict__ rec,
-                                         const DevConst& kc, float (&T)[PPT], float (&cr)[PPT], float (&cg)[PPT],
+                                         const uint32_t* __restrict__ pval, const uint32_t* __restrict__ emit_item,
+                                         const float4* __restrict__ rec, const DevConst& kc, float (&T)[PPT], float (&cr)[PPT], float (&cg)[PPT],
                                          float (&cb)[PPT], uint32_t (&last)[PPT], uint32_t (&amax)[PPT]) {
     constexpr int NT = Layout<TILE, PPT>::kThreads;
     constexpr int kBatch = batch_for(NT);
@@ -293,9 +293,10 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
         for (int i = threadIdx.x; i < kBatch; i += NT) {
             const uint32_t j = bs + i;
             if (j < rg.y) {
-                const uint32_t item = pval[j];
+                const uint32_t pv = pval[j];   // the item, or its emission index (deterministic mode)
+                const uint32_t item = DET ? emit_item[pv] : pv;
                 stage_record(rec, item, g.ox, g.oy, kc.alpha_min, s0[i], s1[i], s2[i]);
-                sid[i] = item;
+                sid[i] = pv;
                 st.mask[i] = warp_mask<TILE, PPT>(g, s0[i], s1[i], s2[i].w);
             }
         }
@@ -346,7 +347,7 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
                 last[p] = bs + k - rg.x + 1;
                 if (ARGMAX && wgt > wmax[p]) {
                     wmax[p] = wgt;
-                    amax[p] = sid[k];
+                    amax[p] = DET ? emit_item[sid[k]] : sid[k];
                 }
             }
         }
@@ -361,12 +362,12 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
 // atomics and one scalar; else a warp sum, then one 9-lane atomic). Each
 // warp visits only the batch entries its compacted list holds, which stop at
 // the warp's largest last-blended entry.
-template <int TILE, int PPT>
+template <int TILE, int PPT, bool DET>
 __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uint32_t* __restrict__ pval,
-                                         const float4* __restrict__ rec, const DevConst& kc, float (&T)[PPT],
-                                         const uint32_t (&cnt_last)[PPT], const float (&gr)[PPT],
-                                         const float (&gg)[PPT], const float (&gb)[PPT],
-                                         float* __restrict__ grad2d) {
+                                         const uint32_t* __restrict__ emit_item, const float4* __restrict__ rec,
+                                         const DevConst& kc, float (&T)[PPT], const uint32_t (&cnt_last)[PPT],
+                                         const float (&gr)[PPT], const float (&gg)[PPT], const float (&gb)[PPT],
+                                         float* __restrict__ grad2d, float* __restrict__ pairgrad) {
     constexpr int NT = Layout<TILE, PPT>::kThreads;
     constexpr int kBatch = batch_for(NT);
     Stage<kBatch, NT / 32>& st = stage<kBatch, NT / 32>();
@@ -401,9 +402,10 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
         for (int i = threadIdx.x; i < kBatch; i += NT) {
             const uint32_t j = bs + i;
             if (j < be) {
-                const uint32_t item = pval[j];
+                const uint32_t pv = pval[j];   // the item, or its emission index (deterministic mode)
+                const uint32_t item = DET ? emit_item[pv] : pv;
                 stage_record(rec, item, g.ox, g.oy, kc.alpha_min, s0[i], s1[i], s2[i]);
-                sid[i] = item;
+                sid[i] = pv;
                 st.mask[i] = warp_mask<TILE, PPT>(g, s0[i], s1[i], s2[i].w);
             }
         }
@@ -469,6 +471,14 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
             }
             const uint32_t who = __ballot_sync(0xFFFFFFFFu, any);
             if (who == 0u) continue;
+            if constexpr (DET) {
+                // deterministic mode (one warp per tile): the warp's fixed-order sum is the
+                // whole tile's contribution; it goes to the pair's own slot, no atomics
+                int idx;
+                const float v = warp_sum9(acc, lane, idx);
+                if (idx >= 0) pairgrad[(size_t)sid[k] * kPairGradStride + idx] = v;
+                continue;
+            }
             if (__popc(who) <= kLaneAtomicMax) {
                 // few lanes blended this Gaussian: each adds its own values (no warp sum)
                 if (any) {
@@ -509,13 +519,13 @@ __device__ __forceinline__ void inside_mask(const TileGeom<TILE, PPT>& g, int wi
     for (int p = 0; p < PPT; ++p) inside[p] = g.px < width && g.py(p) < height;
 }
 
-template <int TILE, int PPT, bool ARGMAX>
+template <int TILE, int PPT, bool ARGMAX, bool DET>
 __global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
     k_raster_fwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ pval, const float4* __restrict__ rec,
                  int width, int height, int tiles_x, int tiles_per_view, int n, DevConst kc,
                  float* __restrict__ out_rgb, float* __restrict__ out_T, uint32_t* __restrict__ out_last,
                  int32_t* __restrict__ out_argmax, uint32_t* __restrict__ queue, uint32_t n_items,
-                 const uint32_t* __restrict__ order) {
+                 const uint32_t* __restrict__ order, const uint32_t* __restrict__ emit_item) {
     int bin;
     const size_t HW = (size_t)width * height;
     while (next_work(queue, n_items, order, bin)) {
@@ -524,7 +534,7 @@ __global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
         inside_mask(g, width, height, inside);
         float T[PPT], cr[PPT], cg[PPT], cb[PPT];
         uint32_t last[PPT], amax[PPT];
-        fwd_core<TILE, PPT, ARGMAX>(g, inside, pval, rec, kc, T, cr, cg, cb, last, amax);
+        fwd_core<TILE, PPT, ARGMAX, DET>(g, inside, pval, emit_item, rec, kc, T, cr, cg, cb, last, amax);
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
             if (!inside[p]) continue;
@@ -541,13 +551,14 @@ __global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
     }
 }
 
-template <int TILE, int PPT>
+template <int TILE, int PPT, bool DET>
 __global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
     k_raster_bwd(const uint2* __restrict__ ranges, const uint32_t* __restrict__ pval, const float4* __restrict__ rec,
                  int width, int height, int tiles_x, int tiles_per_view, DevConst kc,
                  const float* __restrict__ T_final, const uint32_t* __restrict__ n_last,
                  const float* __restrict__ dLdC, float* __restrict__ grad2d, uint32_t* __restrict__ queue,
-                 uint32_t n_items, const uint32_t* __restrict__ order) {
+                 uint32_t n_items, const uint32_t* __restrict__ order, const uint32_t* __restrict__ emit_item,
+                 float* __restrict__ pairgrad) {
     int bin;
     const size_t HW = (size_t)width * height;
     while (next_work(queue, n_items, order, bin)) {
@@ -568,7 +579,7 @@ __global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
                 gb[p] = dLdC[(size_t)g.view * 3 * HW + 2 * HW + pix];
             }
         }
-        bwd_core<TILE, PPT>(g, pval, rec, kc, T, cnt, gr, gg, gb, grad2d);
+        bwd_core<TILE, PPT, DET>(g, pval, emit_item, rec, kc, T, cnt, gr, gg, gb, grad2d, pairgrad);
     }
 }
 
@@ -576,13 +587,15 @@ __global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
 // the L1 term of Eq. 10 and dL/dC = lambda sign(C - I) / 3HW for the tile's
 // pixels, then the adjoint, with final T, last index and dL/dC kept in
 // registers. Writes the image and one photometric partial sum per CTA.
-template <int TILE, int PPT>
+template <int TILE, int PPT, bool DET>
 __global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
     k_raster_fused(const uint2* __restrict__ ranges, const uint32_t* __restrict__ pval,
                    const float4* __restrict__ rec, int width, int height, int tiles_x, int tiles_per_view,
                    DevConst kc, const float* __restrict__ target, const float* const* __restrict__ target_slot,
                    float scale, float* __restrict__ out_rgb, float* __restrict__ grad2d, float* __restrict__ partials,
-                   uint32_t* __restrict__ queue, uint32_t n_items, const uint32_t* __restrict__ order) {
+                   uint32_t* __restrict__ queue, uint32_t n_items, const uint32_t* __restrict__ order,
+                   const uint32_t* __restrict__ emit_item, float* __restrict__ pairgrad,
+                   float* __restrict__ tile_part) {
     if (target_slot != nullptr) target = *target_slot;   // a replayed graph's per-call target
     int bin;
     const size_t HW = (size_t)width * height;
@@ -593,7 +606,8 @@ __global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
         inside_mask(g, width, height, inside);
         float T[PPT], cr[PPT], cg[PPT], cb[PPT], gr[PPT], gg[PPT], gb[PPT];
         uint32_t last[PPT], amax[PPT];
-        fwd_core<TILE, PPT, false>(g, inside, pval, rec, kc, T, cr, cg, cb, last, amax);
+        fwd_core<TILE, PPT, false, DET>(g, inside, pval, emit_item, rec, kc, T, cr, cg, cb, last, amax);
+        float tl = 0.f;   // this thread's photometric sum over the tile
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
             gr[p] = gg[p] = gb[p] = 0.f;
@@ -607,12 +621,27 @@ __global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
             out_rgb[o + HW] = cg[p];
             out_rgb[o + 2 * HW] = cb[p];
             const float r0 = cr[p] - target[o], r1 = cg[p] - target[o + HW], r2 = cb[p] - target[o + 2 * HW];
-            loss += (fabsf(r0) + fabsf(r1)) + fabsf(r2);
+            tl += (fabsf(r0) + fabsf(r1)) + fabsf(r2);
             gr[p] = scale * (float)((r0 > 0.f) - (r0 < 0.f));
             gg[p] = scale * (float)((r1 > 0.f) - (r1 < 0.f));
             gb[p] = scale * (float)((r2 > 0.f) - (r2 < 0.f));
         }
-        bwd_core<TILE, PPT>(g, pval, rec, kc, T, last, gr, gg, gb, grad2d);
+        loss += tl;
+        if constexpr (DET) {
+            // deterministic mode: each tile's sum on its own (fixed tree), whichever CTA took it
+            __shared__ float tred[32];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tl += __shfl_xor_sync(0xFFFFFFFFu, tl, o);
+            if ((threadIdx.x & 31) == 0) tred[threadIdx.x >> 5] = tl;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float t = 0.f;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += tred[w];
+                tile_part[bin] = t * scale;
+            }
+            __syncthreads();
+        }
+        bwd_core<TILE, PPT, DET>(g, pval, emit_item, rec, kc, T, last, gr, gg, gb, grad2d, pairgrad);
     }
     // per-CTA photometric partial (already scaled)
     __shared__ float red[32];
@@ -634,7 +663,8 @@ __global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
 template <int TILE>
 __global__ void __launch_bounds__(TILE* TILE) k_count_work(const uint2* __restrict__ ranges,
                                                            const float4* __restrict__ rec,
-                                                           const uint32_t* __restrict__ pval, int width, int height,
+                                                           const uint32_t* __restrict__ pval,
+                                                           const uint32_t* __restrict__ emit_item, int width, int height,
                                                            int tiles_x, int tiles_per_view, DevConst kc,
                                                            unsigned long long* __restrict__ out) {
     const int bin = blockIdx.x;
@@ -650,7 +680,7 @@ __global__ void __launch_bounds__(TILE* TILE) k_count_work(const uint2* __restri
     float T = 1.f;
     unsigned long long tested = 0, blended = 0, walked = 0;
     for (uint32_t j = rg.x; j < rg.y; ++j) {
-        const uint32_t item = pval[j];
+        const uint32_t item = emit_item != nullptr ? emit_item[pval[j]] : pval[j];
         float4 a, q, c;
         stage_record(rec, item, ox, oy, kc.alpha_min, a, q, c);
         ++tested;
@@ -677,11 +707,11 @@ cudaError_t launch_count_work(gs_ctx* c, const DevConst& k, unsigned long long* 
     if (c->n_bins == 0) return cudaSuccess;
     ++c->launches;
     if (c->tile == 16)
-        k_count_work<16><<<c->n_bins, 256, 0, s>>>(c->ranges, c->rec, c->pval[c->pair_buf], c->width, c->height,
-                                                   c->hcam[0].tiles_x, tpv, k, out);
+        k_count_work<16><<<c->n_bins, 256, 0, s>>>(c->ranges, c->rec, c->pval[c->pair_buf], c->emit_item, c->width,
+                                                   c->height, c->hcam[0].tiles_x, tpv, k, out);
     else
-        k_count_work<8><<<c->n_bins, 64, 0, s>>>(c->ranges, c->rec, c->pval[c->pair_buf], c->width, c->height,
-                                                 c->hcam[0].tiles_x, tpv, k, out);
+        k_count_work<8><<<c->n_bins, 64, 0, s>>>(c->ranges, c->rec, c->pval[c->pair_buf], c->emit_item, c->width,
+                                                 c->height, c->hcam[0].tiles_x, tpv, k, out);
     return cudaGetLastError();
 }
 
@@ -698,57 +728,67 @@ static int resident_grid(K kernel, int threads, int num_sms) {
     return cached;
 }
 
-template <int TILE, int PPT>
+template <int TILE, int PPT, bool DET>
 static void fwd_launch(gs_ctx* c, const DevConst& k, float* rgb, int32_t* argmax, cudaStream_t s, int tpv) {
     constexpr int NT = Layout<TILE, PPT>::kThreads;
     if (argmax) {
-        const int grid = std::min(resident_grid<0, TILE, PPT>(k_raster_fwd<TILE, PPT, true>, NT, c->num_sms), c->n_bins);
-        k_raster_fwd<TILE, PPT, true><<<grid, NT, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width, c->height,
+        const int grid =
+            std::min(resident_grid<0 + 4 * DET, TILE, PPT>(k_raster_fwd<TILE, PPT, true, DET>, NT, c->num_sms), c->n_bins);
+        k_raster_fwd<TILE, PPT, true, DET><<<grid, NT, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width, c->height,
                                                           c->hcam[0].tiles_x, tpv, c->n, k, rgb, c->T_final,
                                                           c->n_last, argmax, c->dcount + 6, (uint32_t)c->n_bins,
-                                                          c->work_order);
+                                                          c->work_order, c->emit_item);
     } else {
         const int grid =
-            std::min(resident_grid<1, TILE, PPT>(k_raster_fwd<TILE, PPT, false>, NT, c->num_sms), c->n_bins);
-        k_raster_fwd<TILE, PPT, false><<<grid, NT, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width,
+            std::min(resident_grid<1 + 4 * DET, TILE, PPT>(k_raster_fwd<TILE, PPT, false, DET>, NT, c->num_sms),
+                     c->n_bins);
+        k_raster_fwd<TILE, PPT, false, DET><<<grid, NT, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width,
                                                            c->height, c->hcam[0].tiles_x, tpv, c->n, k, rgb,
                                                            c->T_final, c->n_last, nullptr, c->dcount + 6,
-                                                           (uint32_t)c->n_bins, c->work_order);
+                                                           (uint32_t)c->n_bins, c->work_order, c->emit_item);
     }
 }
 
-template <int TILE, int PPT>
+template <int TILE, int PPT, bool DET>
 static void bwd_launch(gs_ctx* c, const DevConst& k, const float* dLdC, cudaStream_t s, int tpv) {
     constexpr int NT = Layout<TILE, PPT>::kThreads;
-    const int grid = std::min(resident_grid<2, TILE, PPT>(k_raster_bwd<TILE, PPT>, NT, c->num_sms), c->n_bins);
-    k_raster_bwd<TILE, PPT><<<grid, NT, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width, c->height,
+    const int grid =
+        std::min(resident_grid<2 + 4 * DET, TILE, PPT>(k_raster_bwd<TILE, PPT, DET>, NT, c->num_sms), c->n_bins);
+    k_raster_bwd<TILE, PPT, DET><<<grid, NT, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width, c->height,
                                                 c->hcam[0].tiles_x, tpv, k, c->T_final, c->n_last, dLdC, c->grad2d,
-                                                c->dcount + 7, (uint32_t)c->n_bins, c->work_order);
+                                                c->dcount + 7, (uint32_t)c->n_bins, c->work_order, c->emit_item,
+                                                c->pairgrad);
 }
 
-template <int TILE, int PPT>
+template <int TILE, int PPT, bool DET>
 static void fused_launch(gs_ctx* c, const DevConst& k, const float* target, const float* const* target_slot,
                          float* rgb, cudaStream_t s, int tpv, float* partials, int max_grid, int* grid_out) {
     constexpr int NT = Layout<TILE, PPT>::kThreads;
-    const int grid = std::min(std::min(resident_grid<3, TILE, PPT>(k_raster_fused<TILE, PPT>, NT, c->num_sms),
-                                       c->n_bins), max_grid);
+    const int grid = std::min(
+        std::min(resident_grid<3 + 4 * DET, TILE, PPT>(k_raster_fused<TILE, PPT, DET>, NT, c->num_sms), c->n_bins),
+        max_grid);
     const float scale = k.lambda_color / (float)(3 * (size_t)c->width * c->height);
-    k_raster_fused<TILE, PPT><<<grid, NT, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width, c->height,
+    k_raster_fused<TILE, PPT, DET><<<grid, NT, 0, s>>>(c->ranges, c->pval[c->pair_buf], c->rec, c->width, c->height,
                                                   c->hcam[0].tiles_x, tpv, k, target, target_slot, scale, rgb,
                                                   c->grad2d, partials,
-                                                  c->dcount + 6, (uint32_t)c->n_bins, c->work_order);
+                                                  c->dcount + 6, (uint32_t)c->n_bins, c->work_order, c->emit_item,
+                                                  c->pairgrad, c->tile_part);
     *grid_out = grid;
 }
 
+// The deterministic mode has one layout (8-px tiles, 2 pixels per thread: one
+// warp per tile); the default mode any of the five.
 #define GS_DISPATCH(FN, ...)                                         \
     do {                                                             \
-        if (c->tile == 16) {                                         \
-            if (c->ppt == 1) FN<16, 1>(__VA_ARGS__);                 \
-            else if (c->ppt == 2) FN<16, 2>(__VA_ARGS__);            \
-            else FN<16, 4>(__VA_ARGS__);                             \
+        if (c->cfg.deterministic) {                                  \
+            FN<8, 2, true>(__VA_ARGS__);                             \
+        } else if (c->tile == 16) {                                  \
+            if (c->ppt == 1) FN<16, 1, false>(__VA_ARGS__);          \
+            else if (c->ppt == 2) FN<16, 2, false>(__VA_ARGS__);     \
+            else FN<16, 4, false>(__VA_ARGS__);                      \
         } else {                                                     \
-            if (c->ppt == 1) FN<8, 1>(__VA_ARGS__);                  \
-            else FN<8, 2>(__VA_ARGS__);                              \
+            if (c->ppt == 1) FN<8, 1, false>(__VA_ARGS__);           \
+            else FN<8, 2, false>(__VA_ARGS__);                       \
         }                                                            \
     } while (0)
 

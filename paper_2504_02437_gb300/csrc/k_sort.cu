@@ -319,12 +319,16 @@ __global__ void __launch_bounds__(256) k_tile_scan(const uint32_t* __restrict__ 
 // t0 + j of the run, owned by the last lane whose exclusive count is <= t, so
 // the stores are coalesced and a large Gaussian's pairs are spread over the
 // warp. An item whose pairs would pass pair_cap is skipped and sets *overflow.
+// In the deterministic mode (emit_item != NULL) a pair's value is its emission
+// index e instead of its item, emit_item[e] holds the item, and the pair's
+// gradient slot pairgrad[9 e ..] is cleared.
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order, const uint32_t* __restrict__ tiles,
                                               const uint32_t* __restrict__ off, const float4* __restrict__ rec,
                                               const DevCamera* __restrict__ cams, int n, int tile, uint32_t n_items,
                                               const uint32_t* __restrict__ n_dev, uint64_t pair_cap,
                                               uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval,
-                                              uint32_t* __restrict__ overflow) {
+                                              uint32_t* __restrict__ overflow, uint32_t* __restrict__ emit_item,
+                                              float* __restrict__ pairgrad) {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const uint32_t nv = umin(n_items, *n_dev);
@@ -384,7 +388,14 @@ __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ order
             const uint32_t col = local - row * (uint32_t)s_wt;
             const uint32_t pos = s_o + local;
             pkey[pos] = s_bin0 + (uint32_t)(s_ty0 + (int)row) * s_tx + (uint32_t)(s_tx0 + (int)col);
-            pval[pos] = s_item;
+            if (emit_item != nullptr) {
+                pval[pos] = pos;
+                emit_item[pos] = s_item;
+#pragma unroll
+                for (int q = 0; q < kPairGradStride; ++q) pairgrad[(size_t)pos * kPairGradStride + q] = 0.f;
+            } else {
+                pval[pos] = s_item;
+            }
         }
     }
 }
@@ -499,7 +510,41 @@ cudaError_t emit_pairs(gs_ctx* c, uint32_t n_items, const uint32_t* n_dev, cudaS
     ++c->launches;
     k_emit<<<(n_items + 255) / 256, 256, 0, s>>>(c->dval[0], c->tiles_touched, c->offsets, c->rec, c->dcam, c->n,
                                                  c->tile, n_items, n_dev, (uint64_t)c->pair_cap, c->pkey[0],
-                                                 c->pval[0], c->dcount + 1);
+                                                 c->pval[0], c->dcount + 1, c->emit_item, c->pairgrad);
+    return cudaGetLastError();
+}
+
+// Deterministic mode: item k of the depth order owns the pair slots off[k] ..
+// off[k] + tiles - 1 (its emission indices); their screen gradients are added in
+// that order into the item's grad2d record.
+__global__ void __launch_bounds__(256) k_pairgrad_reduce(const uint32_t* __restrict__ order,
+                                                         const uint32_t* __restrict__ tiles,
+                                                         const uint32_t* __restrict__ off, uint32_t n_items,
+                                                         const uint32_t* __restrict__ n_dev, uint64_t pair_cap,
+                                                         const float* __restrict__ pairgrad,
+                                                         float* __restrict__ grad2d) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_items || k >= *n_dev) return;
+    const uint32_t item = order[k], cnt = tiles[item];
+    const uint64_t o = off[k];
+    float s[kPairGradStride];
+#pragma unroll
+    for (int q = 0; q < kPairGradStride; ++q) s[q] = 0.f;
+    if (cnt != 0 && o + cnt <= pair_cap)
+        for (uint64_t e = o; e < o + cnt; ++e)
+#pragma unroll
+            for (int q = 0; q < kPairGradStride; ++q) s[q] += pairgrad[e * kPairGradStride + q];
+#pragma unroll
+    for (int q = 0; q < kPairGradStride; ++q) grad2d[(size_t)item * kGrad2dStride + q] = s[q];
+}
+
+cudaError_t reduce_pair_grads(gs_ctx* c, cudaStream_t s) {
+    const uint32_t items = (uint32_t)c->n_views * (uint32_t)c->n;
+    if (c->pairgrad == nullptr || items == 0) return cudaSuccess;
+    ++c->launches;
+    k_pairgrad_reduce<<<(items + 255) / 256, 256, 0, s>>>(c->dval[0], c->tiles_touched, c->offsets, items,
+                                                          c->dcount + 8, (uint64_t)c->pair_cap, c->pairgrad,
+                                                          c->grad2d);
     return cudaGetLastError();
 }
 
