@@ -183,7 +183,9 @@ GS_API int gs_step(gs_ctx* ctx, void* stream);
  * target_dev [n_views][3][H][W]; loss_dev optional float[3]; rgb_dev optional
  * output image. With tile_size 0 in the config, the first call for a new
  * (image size, views, map-size bucket) first times the (tile size, pixels per
- * thread) candidates without updating the map and keeps the fastest. An
+ * thread) candidates without updating the map and keeps the fastest (not in
+ * the deterministic mode, which has one layout and adds a fixed-order
+ * per-Gaussian sum of the adjoint's per-pair gradients). An
  * overflow of the pair buffer during a replay skips that iteration's Adam
  * step; a later call then grows the buffer and returns GS_ERR_CAPACITY. */
 GS_API int gs_iterate(gs_ctx* ctx, const gs_camera* cams_host, int n_views, const float* target_dev,
