@@ -33,8 +33,7 @@ Readings of points the paper leaves open (each is a field of ``Config``)
 -----------------------------------------------------------------------
 * colour: k = 3 direct RGB, unclamped; s = exp(log-scale); opacity
   o = sigmoid(logit); the quaternion is normalised inside the forward pass.
-* projection: cull t_z <= near (0.2) and screen positions beyond +-2^23 px or
-  radii beyond 2^22 px; J evaluated at x/z, y/z clamped to
+* projection: cull t_z <= near (0.2); J evaluated at x/z, y/z clamped to
   +-1.3 x the half-FOV tangent (a clamped coordinate carries no gradient);
   low-pass dilation Sigma2D += 0.3 I; largest eigenvalue with the discriminant
   floored at 0.1; integer radius r = ceil(3 sqrt(lambda_max)).
@@ -159,8 +158,6 @@ def project(params, cam, cfg: Config = Config()) -> dict:
     u = cam.fx * tx / tz + cam.cx
     v = cam.fy * ty / tz + cam.cy
     valid = (tz.detach() > cfg.near) & (det.detach() > 0)
-    # screen positions beyond +-2^23 px and radii beyond 2^22 px are culled
-    valid = valid & (u.detach().abs() < 2.0 ** 23) & (v.detach().abs() < 2.0 ** 23) & (r < 2.0 ** 22)
     with torch.no_grad():
         x0, x1, y0, y1 = pixel_box(u, v, r, cam.width, cam.height)
         valid = valid & (x0 <= x1) & (y0 <= y1)

@@ -330,7 +330,7 @@ def test_planar_gradient_closed_form():
     assert np.all(res["grad"][[0, 1, 2, 6, 7, 8, 9, 10, 11, 12, 13]] == 0)
 
 
-def _fd_check(p, cams, tg, rows=None, cols=None, rel_h=1e-5, tol=1e-5):
+def _fd_check(p, cams, tg, rows=None, cols=None, rel_h=1e-6, tol=1e-6):
     """Central differences with h = rel_h max(1, |p|). Bound: tol |g| plus the float64
     rounding of the difference quotient, 100 eps |L| / h."""
     res = O.loss_and_grads(p, cams, tg)
@@ -373,6 +373,59 @@ def test_gradient_finite_differences_tiny(seed, n):
     tg = rng.uniform(size=(1, 3, 16, 16))
     checked, skipped = _fd_check(p, [cam], tg)
     assert checked >= 0.8 * 14 * n
+
+
+def _clamp_scene(front_opacity):
+    """A wide Gaussian in front (sigma about 1,000 px at depth 2, so G > 0.9999 over the 12x12
+    image) and a small one behind it."""
+    return _params([[0.003, -0.002, 2.0], [0.01, 0.005, 3.0]],
+                   [[math.log(20.0), math.log(25.0), math.log(30.0)], [math.log(0.05)] * 3],
+                   [[1, 0.1, -0.2, 0.05], [1, 0, 0.3, 0]], [_logit(front_opacity), 0.0],
+                   [[0.3, 0.6, 0.9], [0.8, 0.2, 0.4]])
+
+
+def test_alpha_clamp_blocks_gradients():
+    """Eq. 3 with alpha = min(0.99, o G): where o G > 0.99 at every pixel the front Gaussian
+    covers, its alpha is the constant 0.99, so the image does not depend on its opacity, scale,
+    rotation or mean. Central differences of the loss are zero for those parameters (to the
+    rounding of the difference quotient), and the oracle's gradient is exactly zero; its colour
+    gradient is lambda / (3HW) sum_p sign(C_p - I_p) 0.99. The same scene with an unclamped front
+    Gaussian (control) has non-zero gradients there, equal to the central differences."""
+    cam = _axis_cam(100.0, 12)
+    cfg = O.Config(lambda_reg=0.0)
+    tg = np.random.default_rng(5).uniform(size=(1, 3, 12, 12))
+    for front, clamped in ((0.9999, True), (0.5, False)):
+        p = _clamp_scene(front)
+        pr = O.project(torch.tensor(p), cam, cfg)
+        py, px = np.meshgrid(np.arange(12), np.arange(12), indexing="ij")
+        res = O.composite(px.ravel(), py.ravel(), pr, cfg)
+        res_all = O.loss_and_grads(p, [cam], tg, cfg)
+        g = res_all["grad"]
+        L = abs(res_all["loss"])
+        # the front Gaussian's o G at every pixel, from its conic
+        with torch.no_grad():
+            dx = torch.tensor(px.ravel(), dtype=torch.float64) - pr["u"][0]
+            dy = torch.tensor(py.ravel(), dtype=torch.float64) - pr["v"][0]
+            oG = pr["o"][0] * torch.exp(-0.5 * (pr["a"][0] * dx * dx + pr["c"][0] * dy * dy) - pr["b"][0] * dx * dy)
+        assert bool((oG > 0.99).all()) == clamped and bool((oG < 0.99).all()) != clamped
+        for i in range(11):
+            h = 1e-6 * max(1.0, abs(p[i, 0]))
+            pp, pm = p.copy(), p.copy()
+            pp[i, 0] += h
+            pm[i, 0] -= h
+            assert O.decision_signature(pp, [cam], cfg) == O.decision_signature(pm, [cam], cfg)
+            fd = (O.loss_value(pp, [cam], tg, cfg) - O.loss_value(pm, [cam], tg, cfg)) / (2 * h)
+            bound = 1e-6 * abs(g[i, 0]) + 100 * np.finfo(float).eps * L / h
+            assert abs(fd - g[i, 0]) <= bound, (i, fd, g[i, 0])
+            if clamped:
+                assert g[i, 0] == 0.0, (i, g[i, 0])
+        if clamped:
+            img = res_all["images"][0]
+            expect = (np.sign(img - tg[0]) * 0.99).sum((1, 2)) / (3 * 12 * 12)
+            np.testing.assert_allclose(g[11:14, 0], expect, rtol=1e-12)
+        else:
+            assert abs(g[10, 0]) > 1e-3 and np.abs(g[0:3, 0]).max() > 1e-6
+        assert int(res["n_contrib"].max()) == 2      # the back Gaussian blends behind it
 
 
 @pytest.mark.slow
@@ -714,14 +767,14 @@ def test_gradient_finite_differences_with_ssim(seed, n):
     checked = 0
     for i in range(14):
         for j in range(n):
-            h = 1e-5 * max(1.0, abs(p[i, j]))
+            h = 1e-6 * max(1.0, abs(p[i, j]))
             pp, pm = p.copy(), p.copy()
             pp[i, j] += h
             pm[i, j] -= h
             if O.decision_signature(pp, [cam]) != base or O.decision_signature(pm, [cam]) != base:
                 continue
             fd = (O.loss_value(pp, [cam], tg, cfg) - O.loss_value(pm, [cam], tg, cfg)) / (2 * h)
-            assert abs(fd - g[i, j]) <= 1e-5 * abs(g[i, j]) + 100 * np.finfo(float).eps * abs(res["loss"]) / h, \
+            assert abs(fd - g[i, j]) <= 1e-6 * abs(g[i, j]) + 100 * np.finfo(float).eps * abs(res["loss"]) / h, \
                 (i, j, fd, g[i, j])
             checked += 1
     assert checked >= 0.8 * 14 * n
