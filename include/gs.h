@@ -178,7 +178,8 @@ GS_API int gs_step(gs_ctx* ctx, void* stream);
  * of n_views keyframes: projection, binning and sort for all views, then one
  * persistent kernel that composites, takes the L1 gradient and runs the
  * adjoint for every (view, tile), then the projection adjoint and Adam. The
- * first call for a shape runs directly (and sizes the pair buffers); it is
+ * first call for a shape runs these kernels directly, synchronising the stream
+ * once after the projection to size the pair buffers; the iteration is then
  * recorded into a CUDA graph that later calls replay with their cameras.
  * target_dev [n_views][3][H][W]; loss_dev optional float[3]; rgb_dev optional
  * output image. With tile_size 0 in the config, the first call for a new
@@ -329,15 +330,20 @@ GS_API int gs_checkpoint_info(const char* path, int* n_host, int* version_host);
  * 8.7 MB) is a static device array that every GPU loading this library
  * holds until the process exits, so n is limited to 1048576 pairs
  * (GS_ERR_CAPACITY above that). keys_in/vals_in ([n] device) are read,
- * keys_out/vals_out ([n] device, distinct from the inputs and from each
- * other) receive the pairs sorted by key, equal keys keeping their input
- * order. Enqueued on `stream` without waiting. The first call on each device
- * resolves the scratch address (call it once before any stream capture).
- * Every call shares the one scratch array, so calls that overlap on the GPU
- * (different streams or host threads) race; the array keeps the last call's
- * contents, and each call writes every word it reads. Errors: GS_ERR_ARG
- * (bits outside 1..32, NULL or aliased buffers), GS_ERR_CAPACITY,
- * GS_ERR_CUDA. */
+ * keys_out/vals_out ([n] device) receive the pairs sorted by the low `bits`
+ * bits of the key (the other bits are kept), equal sort keys keeping their
+ * input order; ceil(bits / 8) radix passes. Neither output range may overlap
+ * an input range or the other output (GS_ERR_ARG); the inputs may overlap.
+ * Enqueued on `stream` without waiting. Each call looks up the array's
+ * address on the current device; the first call on a device loads the
+ * library's device code, so make it before any stream capture. Every call
+ * shares the one scratch array, so calls that overlap on the GPU (different
+ * streams or host threads) race; the array keeps the last call's contents,
+ * and each call writes every word it reads. If the CUDA runtime already holds
+ * an unchecked error from earlier work, the call launches nothing, leaves
+ * that error in place and returns GS_ERR_CUDA. Errors: GS_ERR_ARG (bits
+ * outside 1..32, NULL or overlapping buffers), GS_ERR_CAPACITY, GS_ERR_CUDA
+ * (a failed lookup, memset or launch of this call). */
 GS_API int gs_sort_pairs_static(const uint32_t* keys_in_dev, const uint32_t* vals_in_dev, uint32_t* keys_out_dev,
                                 uint32_t* vals_out_dev, int64_t n, int bits, void* stream);
 

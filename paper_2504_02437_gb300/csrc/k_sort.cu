@@ -14,7 +14,6 @@
 // contiguous slice of the input; element counts are read from device memory so
 // the same launches can sit in a CUDA graph.
 #include <algorithm>
-#include <mutex>
 
 #include "gs_internal.cuh"
 
@@ -575,12 +574,13 @@ constexpr int kStaticSortMaxBlocks = (int)((kStaticSortMaxPairs + 4095u) / 4096u
 constexpr size_t kStaticSortWords = 64                                  // [0] count sentinel
                                     + 2 * (size_t)kStaticSortMaxPairs    // ping-pong keys and values
                                     + 256 * (size_t)kStaticSortMaxBlocks + 256;   // histograms, digit totals
-constexpr int kStaticMaxDevices = 256;
-
 static __device__ __align__(256) uint32_t g_static_sort_scratch[kStaticSortWords];
 
-std::mutex g_static_sort_mutex;
-uint32_t* g_static_sort_addr[kStaticMaxDevices] = {nullptr};
+// [a, a + n) and [b, b + n) words overlap
+bool ranges_overlap(const void* a, const void* b, uint64_t n) {
+    const uint64_t x = (uint64_t)(uintptr_t)a, y = (uint64_t)(uintptr_t)b, len = 4 * n;
+    return x < y + len && y < x + len;
+}
 
 }  // namespace
 }  // namespace gs
@@ -592,20 +592,25 @@ extern "C" int gs_sort_pairs_static(const uint32_t* keys_in, const uint32_t* val
     if (n > (int64_t)kStaticSortMaxPairs) return GS_ERR_CAPACITY;
     if (n == 0) return GS_OK;
     if (!keys_in || !vals_in || !keys_out || !vals_out) return GS_ERR_ARG;
-    if (keys_in == keys_out || vals_in == vals_out || keys_out == vals_out) return GS_ERR_ARG;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return GS_ERR_CUDA;
-    uint32_t* base = nullptr;
-    {
-        // first call on this device: resolve the device address of the scratch array
-        std::lock_guard<std::mutex> lock(g_static_sort_mutex);
-        if (g_static_sort_addr[dev] == nullptr) {
-            void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_static_sort_scratch) != cudaSuccess || p == nullptr) return GS_ERR_CUDA;
-            g_static_sort_addr[dev] = static_cast<uint32_t*>(p);
-        }
-        base = g_static_sort_addr[dev];
+    // a pass reads the inputs while it writes the outputs: no output may overlap an input or the
+    // other output (the inputs may overlap each other)
+    const uint64_t un64 = (uint64_t)n;
+    if (ranges_overlap(keys_out, vals_out, un64) || ranges_overlap(keys_out, keys_in, un64) ||
+        ranges_overlap(keys_out, vals_in, un64) || ranges_overlap(vals_out, keys_in, un64) ||
+        ranges_overlap(vals_out, vals_in, un64))
+        return GS_ERR_ARG;
+    // an unchecked error of earlier work is left for its owner: nothing is launched
+    if (cudaPeekAtLastError() != cudaSuccess) return GS_ERR_CUDA;
+    // The device address of the scratch array on the current device. In host code the array's
+    // name is only a host-side stand-in; the runtime maps it to this device's copy. Resolved on
+    // every call (a lookup once the device code is loaded, which the first call on a device
+    // does), so a context that was reset and re-created gets its own address.
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_sort_scratch) != cudaSuccess || p == nullptr) {
+        cudaGetLastError();   // this call's own error, reported by the return code
+        return GS_ERR_CUDA;
     }
+    uint32_t* base = static_cast<uint32_t*>(p);
     cudaStream_t s = (cudaStream_t)stream;
     uint32_t* sentinel = base;
     uint32_t* tmp_k = base + 64;
@@ -615,7 +620,10 @@ extern "C" int gs_sort_pairs_static(const uint32_t* keys_in, const uint32_t* val
     const int G = (int)std::max<uint32_t>(1u, std::min<uint32_t>((uint32_t)kStaticSortMaxBlocks, (un + 4095u) / 4096u));
     uint32_t* dtot = hist + (size_t)256 * G;
     // the count is passed as n_max with a device-side bound of 0xFFFFFFFF
-    if (cudaMemsetAsync(sentinel, 0xFF, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaMemsetAsync(sentinel, 0xFF, sizeof(uint32_t), s) != cudaSuccess) {
+        cudaGetLastError();
+        return GS_ERR_CUDA;
+    }
     const int passes = (bits + 7) / 8;
     const uint32_t* src_k = keys_in;
     const uint32_t* src_v = vals_in;
@@ -627,10 +635,13 @@ extern "C" int gs_sort_pairs_static(const uint32_t* keys_in, const uint32_t* val
         const int shift = 8 * i;
         const int nb = bits - shift < 8 ? bits - shift : 8;
         k_radix_hist<<<G, kSortThreads, 0, s>>>(src_k, sentinel, un, shift, nb, hist);
+        if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;
         k_digit_scan<<<1 << nb, 256, 0, s>>>(hist, G, dtot);
+        if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;
         k_radix_scatter<<<G, kSortThreads, 0, s>>>(src_k, src_v, dk, dv, sentinel, un, shift, nb, hist, dtot);
+        if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;
         src_k = dk;
         src_v = dv;
     }
-    return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+    return GS_OK;
 }

@@ -6,7 +6,10 @@ rebuilds the order in which gs_render emits its pairs (Gaussians by depth,
 each one's tiles in row-major order) from the render's own sorted pairs, sorts
 that sequence by tile with the static entry point, and requires the render's
 sorted pairs bit for bit, on two scenes in a row and on a repeat of the first
-(the shared scratch keeps the previous call's contents).
+(the shared scratch keeps the previous call's contents). It also sorts seeded
+random keys with 1 to 4 radix passes (bits 7 to 32; the passes in between go
+through the scratch array's ping-pong halves) at sizes up to the 2^20 limit,
+against numpy's stable argsort, larger and smaller inputs back to back.
 """
 import ctypes as C
 
@@ -45,9 +48,14 @@ def _emission_order(bins, vals, depth32):
     return bins[order], vals[order]
 
 
+def _dev_u32(a):
+    """uint32 numpy array -> int32 CUDA tensor with the same bits."""
+    return torch.as_tensor(np.ascontiguousarray(a, np.uint32).view(np.int32), device="cuda")
+
+
 def _static_sort(N, lib, keys, vals, bits):
-    kd = torch.as_tensor(keys.astype(np.int64), device="cuda").to(torch.int32)
-    vd = torch.as_tensor(vals.astype(np.int64), device="cuda").to(torch.int32)
+    kd = _dev_u32(keys)
+    vd = _dev_u32(vals)
     ko = torch.empty_like(kd)
     vo = torch.empty_like(vd)
     s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -71,10 +79,45 @@ def test_static_sort_matches_render_sort_twice():
             np.testing.assert_array_equal(ov, vals)
 
 
+def _expect(keys, vals, bits):
+    mask = np.uint32(0xFFFFFFFF if bits == 32 else (1 << bits) - 1)
+    order = np.argsort(keys & mask, kind="stable")
+    return keys[order], vals[order]
+
+
+@pytest.mark.parametrize("bits", [7, 9, 16, 24, 32])
+def test_static_sort_random_keys_every_pass_count(bits):
+    """1 (bits 7), 2 (9, 16), 3 (24) and 4 (32) radix passes on random keys, some with bits set
+    above `bits` (ignored by the sort, kept in the output), largest size first, then smaller
+    ones: the scratch keeps the previous call's contents."""
+    N, lib = _lib()
+    rng = np.random.default_rng(bits)
+    for n in (1 << 20, 300_000, 4097, 31, 1):
+        keys = rng.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32)
+        if n > 100:
+            keys[: n // 3] &= np.uint32((1 << min(bits, 31)) - 1)   # a third within `bits`
+            keys[n // 3: n // 2] = keys[0]                           # runs of equal keys
+        vals = np.arange(n, dtype=np.uint32) ^ np.uint32(0x5A5A5A5A)
+        ek, ev = _expect(keys, vals, bits)
+        for _ in range(2):          # two calls in a row
+            ok, ov = _static_sort(N, lib, keys, vals, bits)
+            np.testing.assert_array_equal(ok, ek)
+            np.testing.assert_array_equal(ov, ev)
+
+
 def test_static_sort_limits():
     N, lib = _lib()
     null = C.c_void_p()
     s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     assert lib.gs_sort_pairs_static(null, null, null, null, (1 << 20) + 1, 16, s) == N.GS_ERR_CAPACITY
     assert lib.gs_sort_pairs_static(null, null, null, null, 10, 0, s) == N.GS_ERR_ARG
+    assert lib.gs_sort_pairs_static(null, null, null, null, 10, 33, s) == N.GS_ERR_ARG
     assert lib.gs_sort_pairs_static(null, null, null, null, 0, 8, s) == N.GS_OK
+    # outputs that overlap an input or each other are rejected before anything is launched
+    buf = torch.zeros(4 * 64, dtype=torch.int32, device="cuda")
+    a, b, c, d = (C.c_void_p(buf[i * 64:].data_ptr()) for i in range(4))
+    part = C.c_void_p(buf[32:].data_ptr())          # overlaps the second half of a
+    for args in ((a, b, c, a), (a, b, b, d), (a, b, c, c), (a, b, part, d), (a, b, c, part)):
+        assert lib.gs_sort_pairs_static(*args, 64, 16, s) == N.GS_ERR_ARG
+    assert lib.gs_sort_pairs_static(a, a, c, d, 64, 16, s) == N.GS_OK    # inputs may coincide
+    torch.cuda.synchronize()
