@@ -239,6 +239,13 @@ GS_API int gs_mlp_backward(gs_mlp* mlp, const float* feat_dev, const float* targ
                            void* stream);
 /* One Adam step (beta 0.9, 0.999, eps 1e-8) with learning rate lr. */
 GS_API int gs_mlp_step(gs_mlp* mlp, float lr, void* stream);
+/* Training targets of the learned initialiser for the map's Gaussians first ..
+ * first + count - 1: out_dev [count][16] = log-scale (3), the quaternion
+ * normalised with w >= 0 (q and -q are one rotation; a zero quaternion stays
+ * zero), opacity logit (1), colour (3), then five zeros: the output layout of
+ * gs_mlp_forward, for gs_mlp_backward. Errors: GS_ERR_ARG (range outside the
+ * map, NULL out_dev), GS_ERR_CUDA. */
+GS_API int gs_mlp_targets(gs_ctx* ctx, int first, int count, float* out_dev, void* stream);
 /* Make gs_insert initialise new Gaussians with `mlp` (NULL restores the plain
  * initialisation). A point whose prediction is non-finite, has a log-scale
  * outside [-9, 1] or a zero quaternion keeps the plain initialisation. The
@@ -265,6 +272,13 @@ GS_API int gs_densify(gs_ctx* ctx, const float* normals_dev, int* n_split_host, 
  * Gaussian whose count exceeds clarity_sigma (when > 0) and resets the counts.
  * Synchronises. Errors: GS_ERR_ARG, GS_ERR_OOM, GS_ERR_CUDA. */
 GS_API int gs_count_dominant(gs_ctx* ctx, const gs_camera* cams_host, int n_views, void* stream);
+
+/* Peak signal-to-noise ratio of n floats of img_dev against ref_dev (images in
+ * [0, 1]): out_dev[0] = 10 log10(1 / max(MSE, 1e-12)), the evaluation measure
+ * of the time-to-PSNR comparison. Sums in float64 in a fixed order (repeatable
+ * bit for bit); uses the context's scratch, so calls of one context stay on
+ * one stream. Errors: GS_ERR_ARG, GS_ERR_CUDA. */
+GS_API int gs_psnr(gs_ctx* ctx, const float* img_dev, const float* ref_dev, int64_t n, float* out_dev, void* stream);
 
 /* Device-side timing of the path's phases with CUDA events recorded on the
  * launching stream around each phase's kernels (a profiling aid; off by

@@ -838,3 +838,34 @@ def mlp_loss_and_grad(flat, feats, targets, round_bf16: bool = True):
     loss.backward()
     g = torch.cat([l.grad.reshape(-1) for l in leaves]).numpy()
     return float(loss), g
+
+
+def mlp_targets(params) -> np.ndarray:
+    """Training targets of the learned initialiser (its reading: the parameters of converged
+    Gaussians) for params [14, n]: rows [n, 16] = log-scale (3), the quaternion divided by its
+    norm and negated when w < 0 (q and -q are the same rotation), opacity logit, colour (3), and
+    five zeros. A zero quaternion stays zero."""
+    p = np.asarray(params, np.float64)
+    n = p.shape[1]
+    out = np.zeros((n, MLP_OUT_PAD))
+    q = p[ROW_QUAT].T
+    nrm = np.sqrt((q * q).sum(1))
+    sign = np.where(q[:, 0] < 0, -1.0, 1.0)
+    qn = np.where(nrm[:, None] > 0, q * (sign / np.where(nrm > 0, nrm, 1.0))[:, None], 0.0)
+    out[:, 0:3] = p[ROW_LOGSCALE].T
+    out[:, 3:7] = qn
+    out[:, 7] = p[ROW_OPACITY]
+    out[:, 8:11] = p[ROW_RGB].T
+    return out
+
+
+# ------------------------------------------------------------------ evaluation
+
+
+def psnr(img, ref) -> float:
+    """Peak signal-to-noise ratio of images with values in [0, 1]: 10 log10(1 / MSE), the MSE
+    taken over every channel-pixel and floored at 1e-12."""
+    a = np.asarray(img, np.float64)
+    b = np.asarray(ref, np.float64)
+    mse = max(float(np.mean((a - b) ** 2)), 1e-12)
+    return 10.0 * math.log10(1.0 / mse)

@@ -89,6 +89,8 @@ SIGNATURES = {
     "gs_mlp_backward": (_I, [_P, _P, _P, _I, _P, _P]),
     "gs_mlp_step": (_I, [_P, C.c_float, _P]),
     "gs_set_initializer": (_I, [_P, _P]),
+    "gs_mlp_targets": (_I, [_P, _I, _I, _P, _P]),
+    "gs_psnr": (_I, [_P, _P, _P, C.c_int64, _P, _P]),
 }
 PHASES = ("project", "bin", "raster_fwd", "loss", "raster_bwd", "project_bwd", "adam", "raster_fused")
 

@@ -180,6 +180,7 @@ class GaussianMap:
         _f32(loss_out, (3,), "loss_out")
         _f32(rgb_out, (V, 3, H, W), "rgb_out")
         self._check(self.lib.gs_iterate(self.ctx, arr, V, _ptr(target), _ptr(loss_out), _ptr(rgb_out), _stream()))
+        self._last_views, self._last_hw = V, (H, W)
         return loss_out
 
     # ---- map management
@@ -211,6 +212,23 @@ class GaussianMap:
         n = C.c_int()
         self._check(self.lib.gs_densify(self.ctx, _ptr(nz), C.byref(n), _stream()))
         return n.value
+
+    def mlp_targets(self, first: int, count: int) -> torch.Tensor:
+        """Learned-initialiser training targets [count, 16] of Gaussians first .. first + count - 1
+        (log-scale, unit quaternion with w >= 0, opacity logit, colour, zeros)."""
+        out = torch.empty(count, 16, device=f"cuda:{self.device}", dtype=torch.float32)
+        self._check(self.lib.gs_mlp_targets(self.ctx, int(first), int(count), _ptr(out), _stream()))
+        return out
+
+    def psnr(self, img: torch.Tensor, ref: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """10 log10(1 / MSE) of img against ref (same shape, float32, values in [0, 1]) into a
+        device scalar (``out``, a float32 tensor of one element, when given)."""
+        a = _f32(img, tuple(img.shape), "img")
+        b = _f32(ref, tuple(img.shape), "ref")
+        if out is None:
+            out = torch.empty((), device=f"cuda:{self.device}", dtype=torch.float32)
+        self._check(self.lib.gs_psnr(self.ctx, _ptr(a), _ptr(b), a.numel(), _ptr(out), _stream()))
+        return out
 
     # ---- checkpoint / resume
     def save(self, path: str) -> None:

@@ -394,6 +394,7 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
                                                                        cfg->max_views)) == cudaSuccess;
         }
         ok = ok && dalloc(&c->partials, (size_t)c->n_partials + 8) == cudaSuccess;
+        ok = ok && dalloc(&c->psnr_part, (size_t)psnr_scratch_doubles()) == cudaSuccess;
         ok = ok && dalloc(&c->reg_part, (cap + 255) / 256 + 1) == cudaSuccess;
         if (cfg->deterministic) ok = ok && dalloc(&c->tile_part, (size_t)c->max_bins) == cudaSuccess;
         c->n_fpart = 32 * c->num_sms;   // at most 32 resident CTAs per SM
@@ -438,7 +439,7 @@ void gs_destroy(gs_ctx* c) {
     void* ptrs[] = {c->params, c->grads, c->adam_m, c->adam_v, c->dens_sum, c->dens_cnt, c->dom_cnt, c->adam_pw, c->dcam, c->rec,
                     c->tiles_touched, c->depth, c->dkey[0], c->dkey[1], c->dval[0], c->dval[1], c->offsets, c->ranges,
                     c->work_order, c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->vis_blocks, (void*)c->target_slot, c->ssim_maps, c->ssim_part, c->dcount,
-                    c->partials, c->reg_part, c->tile_part, c->fpart,
+                    c->partials, c->psnr_part, c->reg_part, c->tile_part, c->fpart,
                     c->own_rgb};
     for (void* p : ptrs) cudaFree(p);
     free_pairs(c);
@@ -592,6 +593,51 @@ int gs_step(gs_ctx* c, void* stream) {
     return GS_OK;
 }
 
+// Everything of a mapping iteration after the projection and depth sort: binning,
+// compositing + loss + adjoint (one fused kernel with pure L1; forward, SSIM loss and
+// adjoint as three kernels with the SSIM term), the loss total, the projection adjoint
+// and Adam. Shared by the direct first call of gs_iterate and its graph capture; a
+// captured iteration also copies the pair count and overflow flag to the host.
+static int iteration_tail(gs_ctx* c, const DevConst& k, const float* target, const float* const* slot, float* rgb,
+                          float* loss_out, bool capture, cudaStream_t s) {
+    const bool ssim = c->cfg.lambda_photo > 0.f;
+    int cc = back_half(c, k, ssim ? rgb : nullptr, nullptr, s);
+    if (cc != GS_OK) return cc;
+    if (ssim) {
+        Phase ph(c, GS_PHASE_LOSS, s);
+        if (launch_ssim_loss(c, k, rgb, target, slot, c->ssim_part, s) != cudaSuccess ||
+            launch_loss_tail(c, k, c->ssim_part, 2 * ssim_blocks(c->width, c->height, c->n_views), loss_out, s) !=
+                cudaSuccess)
+            return fail(c, GS_ERR_CUDA, "loss launch", cudaGetLastError());
+    }
+    CK(cudaMemsetAsync(c->grad2d, 0, sizeof(float) * kGrad2dStride * c->n_views * (size_t)c->n, s));
+    if (ssim) {
+        Phase ph(c, GS_PHASE_RASTER_BWD, s);
+        CK(launch_raster_backward(c, k, c->dLdC, s));
+    } else {
+        int fgrid = 0;
+        {
+            Phase ph(c, GS_PHASE_RASTER_FUSED, s);
+            CK(launch_raster_fused(c, k, target, slot, rgb, c->fpart, c->n_fpart, &fgrid, s));
+        }
+        Phase ph(c, GS_PHASE_LOSS, s);
+        // the deterministic mode sums the per-tile partials, the default the per-CTA ones
+        const bool det = c->tile_part != nullptr;
+        CK(launch_loss_tail(c, k, det ? c->tile_part : c->fpart, det ? c->n_bins : fgrid, loss_out, s));
+    }
+    {
+        Phase ph(c, GS_PHASE_PROJECT_BWD, s);
+        CK(reduce_pair_grads(c, s));
+        CK(launch_preprocess_backward(c, k, true, s));
+    }
+    {
+        Phase ph(c, GS_PHASE_ADAM, s);
+        CK(launch_adam(c, s));
+    }
+    if (capture) CK(cudaMemcpyAsync(c->hflags, c->dcount, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, s));
+    return GS_OK;
+}
+
 // The autotuner: for each (tile size, pixels per thread) candidate on the
 // caller's views, one plain render sizes the pair buffers, then the part of the
 // mapping iteration that depends on the layout (projection, binning, sort and
@@ -726,8 +772,9 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
         c->rendered_rgb = rgb;
         return GS_OK;
     }
-    // First iteration of this shape: run it directly (sizing the pair buffers), then
-    // record the whole iteration into a graph for the following calls.
+    // First iteration of this shape: the same kernels as a replay, run directly with one
+    // synchronisation after the projection that sizes the pair buffers; then the whole
+    // iteration is recorded into a graph for the following calls.
     drop_graph(c);
     if (c->n == 0) {
         code = gs_render(c, cams, n_views, rgb, nullptr, nullptr, stream);
@@ -736,17 +783,28 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
         if (code == GS_OK) code = gs_step(c, s);
         return code;
     }
-    if ((code = gs_render(c, cams, n_views, rgb, nullptr, nullptr, stream)) != GS_OK) return code;
-    if ((code = gs_loss(c, target, loss_dev, stream)) != GS_OK) return code;
-    if ((code = gs_backward(c, nullptr, stream)) != GS_OK) return code;
-    if ((code = gs_step(c, s)) != GS_OK) return code;
-    const int64_t P = c->pairs_hint;
-    const int64_t want = std::min<int64_t>(P + P / 4 + 4096, kMaxPairs);
-    if (want > c->pair_cap) {
-        CK(cudaStreamSynchronize(s));
-        if (alloc_pairs(c, want) != cudaSuccess) return fail(c, GS_ERR_OOM, "growing the pair buffers failed");
-    }
     const DevConst k = dev_const(c->cfg);
+    c->loss_ready = c->backward_ready = false;
+    b.target = target;
+    ++c->launches;
+    k_set_cams<<<1, 32, 0, s>>>(b, c->dcam, c->target_slot);
+    CK(cudaGetLastError());
+    if ((code = front_half(c, k, s)) != GS_OK) return code;
+    CK(cudaMemcpyAsync(c->hcount, c->dcount, sizeof(uint32_t) * 9, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    {
+        const int64_t P = c->hcount[0];
+        c->visible_hint = c->hcount[8];
+        c->pairs_hint = (uint32_t)std::min<int64_t>(P, 0xFFFFFFFFll);
+        // headroom for the replays' changing cameras
+        const int64_t want = std::min<int64_t>(P + P / 4 + 4096, kMaxPairs);
+        if (P > kMaxPairs) return fail(c, GS_ERR_CAPACITY, "pair count exceeds 2^32");
+        if (want > c->pair_cap && alloc_pairs(c, want) != cudaSuccess)
+            return fail(c, GS_ERR_OOM, "growing the pair buffers failed");
+    }
+    if ((code = iteration_tail(c, k, target, c->target_slot, rgb, loss_out, false, s)) != GS_OK) return code;
+    c->adam_t += 1;
+    c->rendered_rgb = rgb;
     const int64_t launches0 = c->launches;
     c->cap_phases.clear();
     c->capturing = true;
@@ -758,57 +816,10 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
     }
     int cc = GS_OK;
     {
-        DevCamera* dst = c->dcam;
         ++c->launches;
-        b.target = target;
-        k_set_cams<<<1, 32, 0, cs>>>(b, dst, c->target_slot);
+        k_set_cams<<<1, 32, 0, cs>>>(b, c->dcam, c->target_slot);
         cc = front_half(c, k, cs);
-        const bool ssim = c->cfg.lambda_photo > 0.f;
-        // with the SSIM term dL/dC needs the whole image: forward, loss, adjoint as three kernels;
-        // with pure L1 one fused kernel per (view, tile)
-        if (cc == GS_OK) cc = back_half(c, k, ssim ? rgb : nullptr, nullptr, cs);
-        if (cc == GS_OK && ssim) {
-            Phase ph(c, GS_PHASE_LOSS, cs);
-            if (launch_ssim_loss(c, k, rgb, target, c->target_slot, c->ssim_part, cs) != cudaSuccess ||
-                launch_loss_tail(c, k, c->ssim_part, 2 * ssim_blocks(c->width, c->height, c->n_views), loss_out,
-                                 cs) != cudaSuccess)
-                cc = GS_ERR_CUDA;
-        }
-        if (cc == GS_OK &&
-            cudaMemsetAsync(c->grad2d, 0, sizeof(float) * kGrad2dStride * c->n_views * (size_t)c->n, cs) != cudaSuccess)
-            cc = GS_ERR_CUDA;
-        if (cc == GS_OK && ssim) {
-            Phase ph(c, GS_PHASE_RASTER_BWD, cs);
-            if (launch_raster_backward(c, k, c->dLdC, cs) != cudaSuccess) cc = GS_ERR_CUDA;
-        } else if (cc == GS_OK) {
-            int fgrid = 0;
-            {
-                Phase ph(c, GS_PHASE_RASTER_FUSED, cs);
-                if (launch_raster_fused(c, k, target, c->target_slot, rgb, c->fpart, c->n_fpart, &fgrid, cs) !=
-                    cudaSuccess)
-                    cc = GS_ERR_CUDA;
-            }
-            if (cc == GS_OK) {
-                Phase ph(c, GS_PHASE_LOSS, cs);
-                // the deterministic mode sums the per-tile partials, the default the per-CTA ones
-                const bool det = c->tile_part != nullptr;
-                if (launch_loss_tail(c, k, det ? c->tile_part : c->fpart, det ? c->n_bins : fgrid, loss_out, cs) !=
-                    cudaSuccess)
-                    cc = GS_ERR_CUDA;
-            }
-        }
-        if (cc == GS_OK) {
-            Phase ph(c, GS_PHASE_PROJECT_BWD, cs);
-            if (reduce_pair_grads(c, cs) != cudaSuccess || launch_preprocess_backward(c, k, true, cs) != cudaSuccess)
-                cc = GS_ERR_CUDA;
-        }
-        if (cc == GS_OK) {
-            Phase ph(c, GS_PHASE_ADAM, cs);
-            if (launch_adam(c, cs) != cudaSuccess) cc = GS_ERR_CUDA;
-        }
-        if (cc == GS_OK &&
-            cudaMemcpyAsync(c->hflags, c->dcount, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
-            cc = GS_ERR_CUDA;
+        if (cc == GS_OK) cc = iteration_tail(c, k, target, c->target_slot, rgb, loss_out, true, cs);
     }
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(cs, &g);
@@ -862,6 +873,14 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
     c->graph_loss = loss_out;
     c->graph_rgb = rgb;
     c->graph_timing = c->timing;
+    return GS_OK;
+}
+
+int gs_psnr(gs_ctx* c, const float* img_dev, const float* ref_dev, int64_t n, float* out_dev, void* stream) {
+    if (!c) return GS_ERR_ARG;
+    if (n <= 0 || !img_dev || !ref_dev || !out_dev) return fail(c, GS_ERR_ARG, "gs_psnr: bad arguments");
+    CK(cudaSetDevice(c->device));
+    CK(launch_psnr(c, img_dev, ref_dev, (size_t)n, out_dev, (cudaStream_t)stream));
     return GS_OK;
 }
 

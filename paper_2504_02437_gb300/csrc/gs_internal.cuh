@@ -127,6 +127,7 @@ struct gs_ctx {
     uint32_t visible_hint = 0;              // host copy of dcount[8] from the last synchronising render
     uint32_t* hcount = nullptr;             // pinned host mirror
     float* partials = nullptr;              // reduction partials
+    double* psnr_part = nullptr;            // [psnr_scratch_doubles()] partial sums of gs_psnr
     float* reg_part = nullptr;              // [ceil(cap / 256)] planar-term partials of the last projection
     float* fpart = nullptr;                 // photometric partials of the fused kernel (one per CTA)
     int n_fpart = 0;
@@ -208,6 +209,9 @@ cudaError_t launch_loss_tail(gs_ctx* c, const DevConst& k, const float* photo_pa
 cudaError_t launch_loss(gs_ctx* c, const DevConst& k, const float* rgb, const float* target, float* loss_out,
                         cudaStream_t s);
 cudaError_t launch_adam(gs_ctx* c, cudaStream_t s);
+// 10 log10(1 / MSE) of img against ref (n floats each) into out[0] (device)
+cudaError_t launch_psnr(gs_ctx* c, const float* img, const float* ref, size_t n, float* out, cudaStream_t s);
+int psnr_scratch_doubles();
 int ssim_blocks(int width, int height, int n_views);
 cudaError_t launch_ssim_loss(gs_ctx* c, const DevConst& k, const float* rgb, const float* target,
                              const float* const* target_slot, float* partials, cudaStream_t s);

@@ -377,6 +377,34 @@ __global__ void k_apply_mlp(const float* __restrict__ y, const float* __restrict
     for (int c = 0; c < 11; ++c) stage[(size_t)(3 + c) * n + i] = o[c];
 }
 
+// Training target of the learned initialiser for Gaussian `first + i` of the
+// planar [14][cap] parameters: [log-scale (3), unit quaternion with w >= 0
+// (q and -q are the same rotation), opacity logit, colour (3), 0 x 5]. A zero
+// quaternion stays zero.
+__global__ void k_mlp_targets(const float* __restrict__ P, int cap, int first, int count, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const size_t j = (size_t)first + i;
+    const size_t C = (size_t)cap;
+    float* o = out + (size_t)i * kOutPad;
+    const float w = P[6 * C + j], x = P[7 * C + j], y = P[8 * C + j], z = P[9 * C + j];
+    const float nrm = sqrtf(w * w + x * x + y * y + z * z);
+    const float inv = nrm > 0.f ? (w < 0.f ? -1.f : 1.f) / nrm : 0.f;
+    o[0] = P[3 * C + j];
+    o[1] = P[4 * C + j];
+    o[2] = P[5 * C + j];
+    o[3] = w * inv;
+    o[4] = x * inv;
+    o[5] = y * inv;
+    o[6] = z * inv;
+    o[7] = P[10 * C + j];
+    o[8] = P[11 * C + j];
+    o[9] = P[12 * C + j];
+    o[10] = P[13 * C + j];
+#pragma unroll
+    for (int k = kOut; k < kOutPad; ++k) o[k] = 0.f;
+}
+
 }  // namespace
 }  // namespace gs
 
@@ -489,6 +517,16 @@ cudaError_t mlp_forward_rows(gs_mlp* M, const float* feat, int rows, cudaStream_
 // ---------------------------------------------------------------- C ABI
 
 extern "C" {
+
+int gs_mlp_targets(gs_ctx* c, int first, int count, float* out_dev, void* stream) {
+    if (!c || first < 0 || count < 0 || first > c->n || count > c->n - first || (count > 0 && !out_dev))
+        return GS_ERR_ARG;
+    if (count == 0) return GS_OK;
+    if (cudaSetDevice(c->device) != cudaSuccess) return GS_ERR_CUDA;
+    ++c->launches;
+    k_mlp_targets<<<(count + 255) / 256, 256, 0, (cudaStream_t)stream>>>(c->params, c->cap, first, count, out_dev);
+    return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
 
 int gs_mlp_create(int device, uint64_t seed, gs_mlp** out) {
     if (!out) return GS_ERR_ARG;

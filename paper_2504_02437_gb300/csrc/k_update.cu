@@ -122,7 +122,58 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, const float
     if (threadIdx.x == 0) adam_bias_end(st, pw, sbc, spw, gridDim.x);
 }
 
+// PSNR of an image against a reference: per-CTA float64 partial sums of the
+// squared differences (fixed grid, fixed order), then one CTA adds the partials
+// in index order and writes 10 log10(1 / max(MSE, 1e-12)).
+constexpr int kPsnrBlocks = 256;
+__global__ void __launch_bounds__(kRedThreads) k_sqerr(const float* __restrict__ a, const float* __restrict__ b,
+                                                       size_t n, double* __restrict__ part) {
+    __shared__ double sh[kRedThreads / 32];
+    double acc = 0.0;
+    const size_t stride = (size_t)gridDim.x * kRedThreads;
+    for (size_t i = blockIdx.x * (size_t)kRedThreads + threadIdx.x; i < n; i += stride) {
+        const float d = a[i] - b[i];
+        acc += (double)(d * d);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kRedThreads / 32; ++w) t += sh[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_psnr_final(const double* __restrict__ part, int n_part, size_t n,
+                                                            float* __restrict__ out) {
+    __shared__ double sh[kRedThreads / 32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n_part; i += kRedThreads) acc += part[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kRedThreads / 32; ++w) t += sh[w];
+        const double mse = fmax(t / (double)n, 1e-12);
+        out[0] = (float)(10.0 * log10(1.0 / mse));
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_psnr(gs_ctx* c, const float* img, const float* ref, size_t n, float* out, cudaStream_t s) {
+    const int grid = (int)std::min<size_t>((n + kRedThreads - 1) / kRedThreads, (size_t)kPsnrBlocks);
+    c->launches += 2;
+    k_sqerr<<<grid, kRedThreads, 0, s>>>(img, ref, n, c->psnr_part);
+    k_psnr_final<<<1, kRedThreads, 0, s>>>(c->psnr_part, grid, n, out);
+    return cudaGetLastError();
+}
+
+int psnr_scratch_doubles() { return kPsnrBlocks; }
 
 // Planar-term partials of the last projection (view 0's CTAs; none without Gaussians).
 static int reg_partials(const gs_ctx* c) { return (c->n + 255) / 256; }

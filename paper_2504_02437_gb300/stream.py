@@ -22,27 +22,6 @@ from .api import MLP, GaussianMap
 PATCH_CENTRE = slice(36, 39)   # RGB of the centre pixel of the 5x5 patch in the MLP features
 
 
-def psnr(img: torch.Tensor, ref: torch.Tensor) -> torch.Tensor:
-    """10 log10(1 / MSE) of images in [0, 1] (device scalar)."""
-    mse = torch.mean((img - ref) ** 2)
-    return 10.0 * torch.log10(1.0 / torch.clamp(mse, min=1e-12))
-
-
-def canonical_targets(params: torch.Tensor) -> torch.Tensor:
-    """Learned-initialiser targets [n, 16] from Gaussian parameters [14, n]: log-scale, the
-    quaternion normalised with w >= 0, opacity logit, colour; columns 11..15 zero."""
-    p = params.T
-    q = p[:, 6:10]
-    q = q / torch.clamp(q.norm(dim=1, keepdim=True), min=1e-12)
-    q = torch.where(q[:, :1] < 0, -q, q)
-    out = torch.zeros(p.shape[0], 16, device=p.device)
-    out[:, 0:3] = p[:, 3:6]
-    out[:, 3:7] = q
-    out[:, 7] = p[:, 10]
-    out[:, 8:11] = p[:, 11:14]
-    return out
-
-
 def run_stream(gm: GaussianMap, cams: Sequence, targets: torch.Tensor, points: Sequence[torch.Tensor],
                window: int = 8, iters: int = 100, insert: bool = True, densify: bool = True,
                collect: bool = False, track_psnr: str = "", mlp: Optional[MLP] = None,
@@ -104,15 +83,15 @@ def run_stream(gm: GaussianMap, cams: Sequence, targets: torch.Tensor, points: S
                 gm.iterate(wc, wt, loss, rgb)
                 its.append((a, ev()))
                 if curve is not None:
-                    curve[it] = psnr(rgb[-1], targets[j])
+                    gm.psnr(rgb[-1], targets[j], curve[it])
             ev_map.append(its)
             if curve is not None:
                 curves.append(curve)
             elif track_psnr == "final":
-                finals.append(psnr(rgb[-1], targets[j]))
+                finals.append(gm.psnr(rgb[-1], targets[j]))
             if collect and k > 0:
                 xs.append(feats[mask])
-                ys.append(canonical_targets(gm.params()[:, n0:n0 + k]))
+                ys.append(gm.mlp_targets(n0, k))
             d0 = ev()
             if densify:
                 if clarity:

@@ -85,3 +85,30 @@ def test_learned_initialiser_reaches_plain_psnr_sooner():
         gm.close()
     k = S.iterations_to_reach(curves["mlp"], curves["plain"][:, -1]).numpy()
     assert np.mean(np.minimum(k, iters)) <= 0.9 * iters, k
+
+
+def test_psnr_and_training_targets_match_oracle():
+    """gs_psnr and gs_mlp_targets, the stream's evaluation and the initialiser's training
+    targets, against the oracle's definitions."""
+    import oracle as O
+    from paper_2504_02437_gb300.api import GaussianMap
+    rng = np.random.default_rng(4)
+    gm = GaussianMap(capacity=4096, max_views=1, max_width=64, max_height=64)
+    for shape in [(3, 480, 640), (3, 7, 5), (1,)]:
+        a = rng.uniform(size=shape).astype(np.float32)
+        b = np.clip(a + rng.normal(scale=0.05, size=shape), 0, 1).astype(np.float32)
+        got = float(gm.psnr(torch.as_tensor(a, device="cuda"), torch.as_tensor(b, device="cuda")))
+        assert abs(got - O.psnr(a, b)) <= 1e-6 * abs(O.psnr(a, b)), shape
+        assert float(gm.psnr(torch.as_tensor(a, device="cuda"), torch.as_tensor(a, device="cuda"))) == 120.0
+    p = rng.normal(size=(14, 3000)).astype(np.float32)
+    p[6:10, 5] = 0.0                                  # a zero quaternion
+    gm.set_params(torch.as_tensor(p, device="cuda"))
+    for first, count in [(0, 3000), (17, 100), (2999, 1), (5, 0)]:
+        got = gm.mlp_targets(first, count).cpu().numpy()
+        ref = O.mlp_targets(p[:, first:first + count].astype(np.float64))
+        np.testing.assert_allclose(got, ref, rtol=2e-7, atol=2e-7)
+        assert np.all(got[:, 3] >= 0)
+    from paper_2504_02437_gb300._native import GSError
+    with pytest.raises(GSError):
+        gm.mlp_targets(2990, 20)
+    gm.close()
