@@ -70,12 +70,13 @@ def _pack(mean, logscale, quat, opacity_logit, rgb) -> np.ndarray:
 
 def frustum_scene(n: int = 2000, width: int = 160, height: int = 120, fx: float = 150.0,
                   fy: float = 150.0, cx: float = 80.0, cy: float = 60.0, seed: int = 0,
-                  depth_range=(1.0, 5.0), logscale_mean: float = -3.0, logscale_std: float = 0.5):
+                  depth_range=(1.0, 5.0), logscale_mean: float = -3.0, logscale_std: float = 0.5,
+                  opacity_mean: float = 0.0):
     """Gaussians uniform in the frustum of an identity-pose camera.
 
     Depth z ~ U[depth_range]; the image-plane position is uniform over the image
     at that depth; log-scales ~ N(logscale_mean, logscale_std); quaternions are
-    normalised N(0, I4); opacity logits ~ N(0, 1); colours ~ U[0, 1].
+    normalised N(0, I4); opacity logits ~ N(opacity_mean, 1); colours ~ U[0, 1].
     Returns (params [14, n] float32, Camera).
     """
     rng = _rng(seed)
@@ -85,7 +86,7 @@ def frustum_scene(n: int = 2000, width: int = 160, height: int = 120, fx: float 
     mean = np.stack([(px - cx) * z / fx, (py - cy) * z / fy, z], axis=1)
     logscale = rng.normal(logscale_mean, logscale_std, size=(n, 3))
     quat = _random_quats(rng, n)
-    opac = rng.normal(0.0, 1.0, size=n)
+    opac = rng.normal(opacity_mean, 1.0, size=n)
     rgb = rng.uniform(0.0, 1.0, size=(n, 3))
     cam = Camera(width, height, fx, fy, cx, cy)
     return _pack(mean, logscale, quat, opac, rgb), cam

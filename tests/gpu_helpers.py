@@ -10,11 +10,20 @@ from synth import Camera
 # Tolerances of the FP32 CUDA path against the FP64 oracle:
 IMG_ATOL = 1e-4          # max abs pixel error
 GRAD_RTOL = 1e-3         # per-parameter relative gradient error ...
-# ... relative to max(|g*|, GRAD_FLOOR * max |g*| of the parameter group). A gradient is a
-# sum of per-pixel terms that partly cancel; in FP32 its absolute error is ~eps32 times the
-# sum of the terms' magnitudes, measured at <= 2e-7 of the group's largest gradient. The floor
-# holds gradients below 1e-3 of that largest to an absolute error of 1e-6 of it instead.
-GRAD_FLOOR = 1e-3
+# ... relative to max(|g*|, GRAD_FLOOR * max |g*| of the parameter group). A gradient is a sum of
+# per-pixel terms that partly cancel; in FP32 its absolute error is ~eps32 times the sum of the
+# terms' magnitudes. Measured on the parity scenes (every compositing layout, the deterministic
+# mode, single and multi-view): |g - g*| <= 1.8e-6 of the group's largest gradient, and the
+# smallest floor under which every gradient passes is 7.4e-5 of it; GRAD_FLOOR keeps a margin
+# of 2.7 over that. The deep-list scene (pixels blending several hundred Gaussians) sums
+# correspondingly more terms: it needs 4.4e-4, and GRAD_FLOOR_DEEP keeps a margin of 2.3.
+GRAD_FLOOR = 2e-4
+GRAD_FLOOR_DEEP = 1e-3
+# Screen-space gradients of one view (du, dv, conic, opacity, colour per Gaussian) are sums over
+# fewer, more strongly cancelling pixel terms than the parameter gradients (which add all views
+# and the projection's chain): one rotated view of the three-view window needs 2.4e-4 of the
+# group's largest gradient; SCREEN_GRAD_FLOOR keeps a margin of 4.
+SCREEN_GRAD_FLOOR = 1e-3
 GROUPS = {"mean": slice(0, 3), "logscale": slice(3, 6), "quat": slice(6, 10), "opacity": slice(10, 11),
           "rgb": slice(11, 14)}
 
@@ -28,13 +37,15 @@ def cuda(x):
     return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float32, device="cuda")
 
 
-def grad_errors(g_gpu, g_ref, exclude=None):
-    """Per-group max relative error |g - g*| / max(|g*|, GRAD_FLOOR max_group |g*|) over non-excluded Gaussians."""
+def grad_errors(g_gpu, g_ref, exclude=None, floor_frac=None):
+    """Per-group max relative error |g - g*| / max(|g*|, floor_frac max_group |g*|) over non-excluded
+    Gaussians (floor_frac defaults to GRAD_FLOOR)."""
+    floor_frac = GRAD_FLOOR if floor_frac is None else floor_frac
     out = {}
     keep = np.ones(g_ref.shape[1], bool) if exclude is None else ~exclude
     for name, sl in GROUPS.items():
         a, b = g_gpu[sl][:, keep], g_ref[sl][:, keep]
-        floor = GRAD_FLOOR * max(np.abs(g_ref[sl]).max(), 1e-30)
+        floor = floor_frac * max(np.abs(g_ref[sl]).max(), 1e-30)
         rel = np.abs(a - b) / np.maximum(np.abs(b), floor)
         out[name] = float(rel.max()) if rel.size else 0.0
     return out
@@ -57,3 +68,15 @@ def rotated_cam(base: Camera, rotvec, shift) -> Camera:
 def oracle_project_np(p, cam):
     pr = O.project(torch.as_tensor(p, dtype=torch.float64), cam)
     return {k: (v.detach().numpy() if torch.is_tensor(v) else v) for k, v in pr.items()}
+
+
+def exclude_kernel_limits(p64, cams):
+    """Gaussians outside the float32 range of the kernels' pixel-box arithmetic in some view: a
+    screen mean beyond +-2^23 px or an integer radius beyond 2^22 px (the kernels cull them; the
+    oracle has no such limit). The parity tests leave them out of the comparison."""
+    out = np.zeros(p64.shape[1], bool)
+    for cam in cams:
+        pr = oracle_project_np(p64, cam)
+        ok = pr["valid"]
+        out |= ok & ((np.abs(pr["u"]) >= 2.0 ** 23) | (np.abs(pr["v"]) >= 2.0 ** 23) | (pr["r"] >= 2.0 ** 22))
+    return out

@@ -5,8 +5,9 @@ Small single-view workload: 2,000 frustum Gaussians, 160x120, fx = fy = 150
 compared bit-exactly (the oracle's binning is fed the kernel's FP32 screen
 quantities); images within 1e-4 absolute away from pixels where a discrete
 decision lies within FP32 rounding of its threshold; gradients within 1e-3
-relative (floored at 1e-3 of the group's largest gradient, the FP32 accumulation
-level of these cancelling sums).
+relative, floored at a fraction of the group's largest gradient set from the
+measured FP32 accumulation error of these cancelling sums (2e-4 for parameter
+gradients, 1e-3 for one view's screen-space gradients; tests/gpu_helpers.py).
 """
 import numpy as np
 import pytest
@@ -15,7 +16,7 @@ import torch
 import oracle as O
 from synth import Camera, frustum_scene, random_target
 
-from gpu_helpers import (GRAD_FLOOR, GRAD_RTOL, IMG_ATOL, cuda, grad_errors, new_map, oracle_project_np,
+from gpu_helpers import (GRAD_RTOL, IMG_ATOL, SCREEN_GRAD_FLOOR, cuda, grad_errors, new_map, oracle_project_np,
                          rotated_cam)
 
 pytestmark = pytest.mark.gpu
@@ -120,12 +121,12 @@ def test_screen_gradients_match_oracle(ref, gpu_run):
     names = ["u", "v", "a", "b", "c", "o"]
     for k, name in enumerate(names):
         ref_k = g2[name]
-        floor = GRAD_FLOOR * np.abs(ref_k).max()
+        floor = SCREEN_GRAD_FLOOR * np.abs(ref_k).max()
         rel = np.abs(gpu[k] - ref_k)[keep] / np.maximum(np.abs(ref_k[keep]), floor)
         assert rel.max() <= GRAD_RTOL, (name, rel.max())
     for c in range(3):
         ref_k = g2["rgb"][:, c]
-        floor = GRAD_FLOOR * np.abs(ref_k).max()
+        floor = SCREEN_GRAD_FLOOR * np.abs(ref_k).max()
         rel = np.abs(gpu[6 + c] - ref_k)[keep] / np.maximum(np.abs(ref_k[keep]), floor)
         assert rel.max() <= GRAD_RTOL, ("rgb", c, rel.max())
 
