@@ -99,11 +99,16 @@ WINDOW_TRAJECTORY_SEED = 33
 
 
 def make_window_workload(seed: int = 0, n_views: int = 8, n_gauss: int = 150_000,
-                         trajectory_seed: int = WINDOW_TRAJECTORY_SEED):
+                         trajectory_seed: int = WINDOW_TRAJECTORY_SEED, device=None):
+    """(params, cameras, targets [V, 3, 480, 640]); with ``device`` the targets are ray-cast on
+    that GPU (the same formula as the CPU ray-cast) and returned as a device tensor."""
     from synth import make_room, room_gaussians, room_trajectory
     room = make_room(seed)
     cams = room_trajectory(n_views, trajectory_seed, 640, 480, 525.0, 525.0)
     params = room_gaussians(room, n_gauss, seed)
+    if device is not None:
+        import torch
+        return params, cams, torch.stack([room.raycast_torch(c, device) for c in cams]).contiguous()
     cache = os.path.join(tempfile.gettempdir(), f"gs_room_window_{seed}_{trajectory_seed}_{n_views}.npy")
     if os.path.exists(cache):
         targets = np.load(cache)
@@ -221,57 +226,150 @@ def replica_throughput(steps: int, world: int, slowest_ms: float) -> float:
 # --------------------------------------------------------------------------- CPU oracle
 
 
-def oracle_sample(params, cam, target, n_tiles: int, seed: int):
-    """Oracle fwd+bwd+Adam on ``n_tiles`` random 16x16 pixel tiles of the workload.
+TILE_GRID = (16, 8)     # 128 sample tiles of 16x16 px, evenly spread over the image
 
-    Returns (seconds, fraction of the full image's pixels covered).
-    """
-    import torch
-    import oracle as O
-    rng = np.random.default_rng(seed)
+
+def sample_tiles() -> list:
+    """Origins of 128 sample tiles on a 16 x 8 grid over the image, in bit-reversed order so
+    that any prefix of the list is spread over the whole image. Every CPU-oracle sample of
+    this benchmark takes its tiles from this list."""
+    gx, gy = TILE_GRID
+    cells = [(int(round((i + 0.5) * (W - 16) / gx)), int(round((j + 0.5) * (H - 16) / gy)))
+             for j in range(gy) for i in range(gx)]
+    bits = (len(cells) - 1).bit_length()
+    rev = sorted(range(len(cells)), key=lambda k: int(format(k, f"0{bits}b")[::-1], 2))
+    return [cells[k] for k in rev]
+
+
+def _tile_pixels(tiles) -> np.ndarray:
     pix = []
-    for _ in range(n_tiles):
-        x0 = int(rng.integers(0, W - 16))
-        y0 = int(rng.integers(0, H - 16))
+    for x0, y0 in tiles:
         yy, xx = np.mgrid[y0:y0 + 16, x0:x0 + 16]
         pix.append(np.stack([xx.ravel(), yy.ravel()], 1))
-    pix = np.concatenate(pix)
+    return np.concatenate(pix) if pix else np.zeros((0, 2), np.int64)
+
+
+def oracle_step(params, cam, target, tiles) -> float:
+    """Seconds of one oracle mapping iteration restricted to the 16x16 pixel tiles at the
+    origins ``tiles``: projection of all Gaussians, compositing and L1 of those pixels, the
+    adjoint of both, the planar term and Adam. With no tiles it is the part of an iteration
+    that does not depend on the pixels (projection, its adjoint, planar term, Adam)."""
+    import oracle as O
+    pix = _tile_pixels(tiles)
     p64 = params.astype(np.float64)
     t0 = time.perf_counter()
     res = O.loss_and_grads(p64, [cam], target[None], pixels=[pix], chunk=256)
     O.adam_step(p64, res["grad"], np.zeros_like(p64), np.zeros_like(p64), 1)
-    dt = time.perf_counter() - t0
-    return dt, pix.shape[0] / float(W * H), torch.get_num_threads()
+    return time.perf_counter() - t0
+
+
+FULL_TILES = W * H / 256.0     # the image's area in 16x16 tiles
+
+
+def oracle_full_iteration_s(t_fixed: float, t_sample: float, n_tiles: int) -> float:
+    """A full iteration's oracle time from its pixel-independent part and a sample of tiles:
+    t_fixed + (t_sample - t_fixed) / n_tiles x (W H / 256)."""
+    return t_fixed + max(t_sample - t_fixed, 0.0) / n_tiles * FULL_TILES
+
+
+def _cpu_model() -> str:
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu model")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_oracle_baseline(params, cam, target, tiles_all: int, tiles_single: int) -> dict:
+    """The FP64 oracle (as it stands) on the host cores, all of them and one: the Replica-shaped
+    iteration from its pixel-independent part (median of 3 after a warm-up call) plus the first
+    tiles of the sample-tile list, and the small single-view workload (2,000 Gaussians, 160x120)
+    timed in full."""
+    import torch
+    import oracle as O
+    from synth import frustum_scene, random_target
+    n_all = torch.get_num_threads()
+    p1, c1 = frustum_scene()
+    tg1 = random_target(160, 120, seed=1)
+    p1 = p1.astype(np.float64)
+    grid = sample_tiles()
+    out = {"cpu_model": _cpu_model(), "nproc": os.cpu_count()}
+    try:
+        for label, nth, n_t in (("all_cores", n_all, tiles_all), ("single_thread", 1, tiles_single)):
+            torch.set_num_threads(nth)
+            oracle_step(params, cam, target, [])
+            t_fixed = statistics.median(oracle_step(params, cam, target, []) for _ in range(3))
+            tiles = grid[:n_t]
+            t_sample = oracle_step(params, cam, target, tiles)
+            full = oracle_full_iteration_s(t_fixed, t_sample, len(tiles))
+            t0 = time.perf_counter()
+            r = O.loss_and_grads(p1, [c1], tg1)
+            O.adam_step(p1, r["grad"], np.zeros_like(p1), np.zeros_like(p1), 1)
+            t_small = time.perf_counter() - t0
+            out[label] = {"threads": nth, "replica_iters_per_s": 1.0 / full, "replica_full_iteration_s": full,
+                          "fixed_s": t_fixed, "tiles_sampled": len(tiles),
+                          "per_tile_s": (t_sample - t_fixed) / len(tiles),
+                          "small_2k_160x120_iters_per_s": 1.0 / t_small, "small_2k_160x120_s": t_small}
+    finally:
+        torch.set_num_threads(n_all)
+    return out
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores, on the GPU arm's workload, metric and unit: each
+    step is one bounded sample (all Gaussians, 4 random 16x16 tiles); the full-iteration rate
+    comes from the pixel-independent part (timed in the warm-up) plus the steps' mean per-tile
+    time. ms_per_step is the measured time of a sample step."""
+    import torch
     world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
     if rank != 0:
         return 0
     params, cam, target = make_workload(0)
     tiles_per_step = 4
-    for w in range(args.warmup):
-        oracle_sample(params, cam, target, 1, 1000 + w)
-    secs, frac = 0.0, 0.0
-    cores = 1
-    for k in range(args.steps):
-        dt, f, cores = oracle_sample(params, cam, target, tiles_per_step, k)
-        secs += dt
-        frac += f
-    value = frac / secs                    # full iterations per second
-    sample = (f"{args.steps} steps x {tiles_per_step} random 16x16 tiles ({tiles_per_step * 256} of {W * H} pixels) "
-              f"of the full workload: FP64 fwd+bwd over all 300k Gaussians + Adam, scaled by pixel fraction")
+    grid = sample_tiles()
+    # warm-up steps: the pixel-independent part alone (the first call also warms the thread pool)
+    fixed = [oracle_step(params, cam, target, []) for w in range(args.warmup)]
+    t_fixed = statistics.median(fixed[1:] if len(fixed) > 1 else fixed)
+    steps = [oracle_step(params, cam, target, [grid[(k * tiles_per_step + i) % len(grid)]
+                                               for i in range(tiles_per_step)]) for k in range(args.steps)]
+    t_step = statistics.mean(steps)
+    full = oracle_full_iteration_s(t_fixed, t_step, tiles_per_step)
+    value = 1.0 / full
+    cores = torch.get_num_threads()
+    sample = (f"each step: FP64 fwd+bwd of all 300k Gaussians on {tiles_per_step} 16x16 tiles "
+              f"({tiles_per_step * 256} of {W * H} pixels; step k takes tiles 4k..4k+3 of a fixed list of 128 "
+              f"spread over the image) + Adam, {t_step:.2f} s; full iteration = pixel-independent part "
+              f"{t_fixed:.2f} s (median of the warm-up steps after the first, no pixels) + mean per-tile time "
+              f"x {FULL_TILES:.1f} tiles = {full:.1f} s")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": W, "height": H},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "full_iteration_s": full,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": _cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
 # --------------------------------------------------------------------------- GPU path
+
+
+def fused_roofline(work: dict, ms: float, n_sm: int, peaks: dict) -> dict:
+    """The compositing kernel against the FP32 peak: algorithmic FLOPs of the render's pairs
+    (tested, blended, walked; ``gs_debug_work``) over its measured duration."""
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    flops = (FLOP_FWD_TESTED * work["tested"] + FLOP_FWD_BLENDED * work["blended"]
+             + FLOP_BWD_WALKED * work["walked"] + FLOP_BWD_BLENDED * work["blended"])
+    ach = flops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "flop_per_launch": flops, "ms_per_launch": ms,
+            "peak_source": "FP32 lanes x 2 x SMs x max SM clock"}
 
 
 def run_ours(args):
@@ -295,10 +393,9 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    # warm-up with every phase timed (the per-phase breakdown). The first call runs the iteration
-    # as separate kernels (render, loss, adjoint: phases that the replays do not have) and
-    # captures its graph; its records are dropped, so the breakdown and the dominant phase
-    # come from graph replays only
+    # warm-up with every phase timed (the per-phase breakdown): the first call runs the iteration
+    # directly and captures its graph; its records are dropped, so the breakdown and the dominant
+    # phase come from graph replays only
     gm.timing(True)
     gm.iterate(cam, tgt, loss)
     torch.cuda.synchronize()
@@ -309,32 +406,36 @@ def run_ours(args):
     phases_all = gm.timing_read()
     per_all = {k: v[0] / v[1] for k, v in phases_all.items() if v[1] > 0}
     dom = max(per_all, key=per_all.get)
-    # the timed region records events around the dominant kernel only (each timed phase adds
+    # the timed regions record events around the dominant kernel only (each timed phase adds
     # event nodes to the replayed graph); the changed graph is captured in two more warm-ups
     gm.timing(True, phases=[dom])
     for _ in range(2):
         gm.iterate(cam, tgt, loss)
     torch.cuda.synchronize()
 
-    # ---- device-resident timed region (L2 flushed between iterations)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # ---- device-resident timed regions: `repeats` regions of exactly `steps` iterations each,
+    # L2 flushed between iterations; the median region is the headline
+    R = max(1, args.repeats)
     gm.timing(True, phases=[dom])      # clears the warm-up records, same mask: the graph stays
     launches0 = gm.launches
+    region_ms = []
     with ClockSampler(local) as clk:
-        barrier(world)
-        torch.cuda.synchronize()
-        for k in range(args.steps):
-            flush.zero_()
-            starts[k].record(stream)
-            gm.iterate(cam, tgt, loss)
-            ends[k].record(stream)
-        torch.cuda.synchronize()
-        barrier(world)
-    launches = gm.launches - launches0
+        for r in range(R):
+            starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            barrier(world)
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                flush.zero_()
+                starts[k].record(stream)
+                gm.iterate(cam, tgt, loss)
+                ends[k].record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+            region_ms.append(max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(starts, ends)), world))
+    launches = (gm.launches - launches0) // R
     phases = gm.timing_read()
-    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    total_ms = max_over_ranks(total_ms, world)
+    total_ms = statistics.median(region_ms)
     ms_per_step = total_ms / args.steps
     value = replica_throughput(args.steps, world, total_ms)
     final_loss = loss.cpu().numpy().tolist()
@@ -362,52 +463,41 @@ def run_ours(args):
         copy_stream.wait_event(free[k % 2])
         h2d(bufs[k % 2], tgt_host, copy_stream)
         ready[k % 2].record(copy_stream)
-    for e in free:
-        e.record(stream)
-    e_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    e_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    barrier(world)
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.zero_()
-        e_s[k].record(stream)
-        if k == 0:
-            copy_stream.wait_event(e_s[0])
-            upload(0)
-        if k + 1 < args.steps:
-            upload(k + 1)
-        stream.wait_event(ready[k % 2])
-        gm.iterate(cam, bufs[k % 2], loss)
-        free[k % 2].record(stream)
-        loss_host.copy_(loss, non_blocking=True)
-        e_e[k].record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(e_s, e_e)), world)
-    e2e_value = replica_throughput(args.steps, world, e2e_ms)
+    e2e_region_ms = []
+    for r in range(R):
+        for e in free:
+            e.record(stream)
+        e_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        e_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            e_s[k].record(stream)
+            if k == 0:
+                copy_stream.wait_event(e_s[0])
+                upload(0)
+            if k + 1 < args.steps:
+                upload(k + 1)
+            stream.wait_event(ready[k % 2])
+            gm.iterate(cam, bufs[k % 2], loss)
+            free[k % 2].record(stream)
+            loss_host.copy_(loss, non_blocking=True)
+            e_e[k].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        e2e_region_ms.append(max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(e_s, e_e)), world))
+    e2e_value = replica_throughput(args.steps, world, statistics.median(e2e_region_ms))
 
     # ---- roofline of the dominant kernel
     work = gm.debug_work()
-    # the dominant kernel in the timed region (the warm-up replays' figure if no timed step
+    # the dominant kernel in the timed regions (the warm-up replays' figure if no timed step
     # recorded it, e.g. a step that re-captured the graph)
     per = {k: (v[0] / v[1] if v[1] > 0 else per_all.get(k, 0.0)) for k, v in phases.items()}
     peaks, peak_src = _peaks()
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    fp32_peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     if dom == "raster_fused":
-        flops = (FLOP_FWD_TESTED * work["tested"] + FLOP_FWD_BLENDED * work["blended"]
-                 + FLOP_BWD_WALKED * work["walked"] + FLOP_BWD_BLENDED * work["blended"])
-        roof = {"bound": "alu", "achieved": flops / (per[dom] * 1e-3) / 1e12, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s"}
-    elif dom == "raster_bwd":
-        flops = FLOP_BWD_WALKED * work["walked"] + FLOP_BWD_BLENDED * work["blended"]
-        roof = {"bound": "alu", "achieved": flops / (per[dom] * 1e-3) / 1e12, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s"}
-    elif dom == "raster_fwd":
-        flops = FLOP_FWD_TESTED * work["tested"] + FLOP_FWD_BLENDED * work["blended"]
-        roof = {"bound": "alu", "achieved": flops / (per[dom] * 1e-3) / 1e12, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s"}
+        roof = fused_roofline(work, per[dom], n_sm, peaks)
     else:
         # memory-bound phases: algorithmic bytes per unit (see the design notes' table)
         P, N = work["pairs"], gm.n
@@ -415,62 +505,71 @@ def run_ours(args):
                        "loss": 3 * 4 * 3 * W * H, "project_bwd": 56 * N + 48 * N + 56 * N,
                        "adam": 14 * N * 4 * 7}
         roof = {"bound": "hbm", "achieved": bytes_model[dom] / (per[dom] * 1e-3) / 1e9,
-                "peak": float(peaks["hbm_gbs"]), "unit": "GB/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+                "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = _ncu_traffic(dom, gm.tile_size, gm.pixels_per_thread)
     roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
     roof["kernel"] = dom
-    roof["peak_source"] = ("FP32 lanes x 2 x SMs x max SM clock" if roof["bound"] == "alu"
-                           else f"MEASURED_PEAKS.json hbm_gbs ({peak_src})")
+    layout = {"tile": gm.tile_size, "pixels_per_thread": gm.pixels_per_thread}
+    gm.close()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": W, "height": H,
-                       "tile": gm.tile_size, "pixels_per_thread": gm.pixels_per_thread, "l2": "flushed between iterations (256 MB write)",
-                       "parallelism": f"replicas x{world}"},
+                       "l2": "flushed between iterations (256 MB write)", "parallelism": f"replicas x{world}"},
+            "repeats": R,
+            "value_spread": {"min": replica_throughput(args.steps, world, max(region_ms)),
+                             "max": replica_throughput(args.steps, world, min(region_ms)),
+                             "what": f"{R} timed regions of {args.steps} iterations each; value is the median"},
+            "layout": layout,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(tgt.numel() * 4),
                     "d2h_bytes_per_step": 12,
                     "how": "target uploaded from pinned host memory on a copy stream (step k+1's during step k), "
-                           "loss read back to pinned memory, each step bracketed, L2 flushed between steps"},
+                           "loss read back to pinned memory, each step bracketed, L2 flushed between steps; "
+                           f"median of {R} regions"},
             "gpu_launches": int(launches),
             "roofline": roof,
             "clocks": clk.summary(),
             "phases_ms": {k: round(v, 5) for k, v in per_all.items()},
             "phases_note": "per-phase device ms from the warm-up graph replays with every phase timed",
             "work": work, "final_loss": final_loss}
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["window"] = window_measure(args, max(args.steps, 20), local)
+        line["learned_init"] = learned_init_measure(args, local)
     if rank == 0 and world == 1 and not args.no_cpu:
-        dt, frac, cores = oracle_sample(params, cam, target, args.cpu_tiles, 7)
-        line["cpu_baseline"] = {"value": frac / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{args.cpu_tiles} random 16x16 tiles ({args.cpu_tiles * 256} of {W * H} "
-                                          f"pixels): FP64 fwd+bwd over all 300k Gaussians + Adam, "
-                                          f"{dt:.1f} s, scaled by pixel fraction"}
+        cb = cpu_oracle_baseline(params, cam, target, args.cpu_tiles, args.cpu_tiles_single)
+        a = cb["all_cores"]
+        line["cpu_baseline"] = {
+            "value": a["replica_iters_per_s"], "unit": UNIT, "cores": a["threads"], "kind": "oracle",
+            "sample": (f"FP64 oracle on {a['threads']} host threads ({cb['cpu_model']}, nproc {cb['nproc']}): "
+                       f"pixel-independent part of an iteration (projection of all 300k Gaussians, its adjoint, "
+                       f"planar term, Adam) {a['fixed_s']:.2f} s + {a['tiles_sampled']} 16x16 tiles spread over the "
+                       f"image at {a['per_tile_s']:.3f} s each, scaled to the {FULL_TILES:.1f} tiles of the image"),
+            "variants": cb}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    gm.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
 
 
-def run_window(args):
-    """Window workload: one call renders and back-propagates all 8 views (one persistent
-    compositing launch in the replayed graph) vs 8 single-view iterations, same GPU."""
+def window_measure(args, steps: int, device: int = 0) -> dict:
+    """The keyframe window (8 views 640x480, 150k Gaussians): iterations/s of one call that renders
+    and back-propagates all views in one persistent compositing launch (replayed graph), against
+    the same work as 8 single-view iterations, plus the compositing kernel's FP32 roofline."""
     import torch
-    torch.cuda.set_device(0)
-    from paper_2504_02437_gb300 import build as B
-    B.build()
     from paper_2504_02437_gb300.api import GaussianMap
-    params, cams, targets = make_window_workload(0)
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", device)
+    params, cams, tgt = make_window_workload(0, device=dev)
     V = len(cams)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    tgt = torch.as_tensor(targets, device=dev).contiguous()
     stream = torch.cuda.current_stream()
 
-    def timed(fn, steps):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    def timed(fn, n):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
         torch.cuda.synchronize()
         for a, b in ev:
             flush.zero_()
@@ -478,58 +577,73 @@ def run_window(args):
             fn()
             b.record(stream)
         torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in ev) / steps
+        return sum(a.elapsed_time(b) for a, b in ev) / n
 
-    gm = GaussianMap(capacity=params.shape[1], max_views=V, max_width=640, max_height=480, tile_size=args.tile,
-                     pixels_per_thread=args.ppt)
+    gm = GaussianMap(capacity=params.shape[1], max_views=V, max_width=640, max_height=480, device=device,
+                     tile_size=args.tile, pixels_per_thread=args.ppt)
     gm.set_params(torch.as_tensor(params, device=dev))
     loss = torch.empty(3, device=dev)
-    gm.timing(True)
-    gm.iterate(cams, tgt, loss)        # runs the iteration as separate kernels and captures its graph
-    torch.cuda.synchronize()
-    gm.timing(True)                    # drops those records: the breakdown comes from replays
-    for _ in range(max(args.warmup - 1, 2)):
+    for _ in range(max(args.warmup, 3)):
         gm.iterate(cams, tgt, loss)
-    torch.cuda.synchronize()
-    phases = gm.timing_read()          # breakdown from the warm-up replays, every phase timed
-    gm.timing(False)                   # the timed region runs the graph without event nodes
+    gm.timing(True, phases=["raster_fused"])
     for _ in range(2):
         gm.iterate(cams, tgt, loss)
+    torch.cuda.synchronize()
+    gm.timing(True, phases=["raster_fused"])
     l0 = gm.launches
-    with ClockSampler(0) as clk:
-        ms_window = timed(lambda: gm.iterate(cams, tgt, loss), args.steps)
-    launches = gm.launches - l0
+    with ClockSampler(device) as clk:
+        ms_window = timed(lambda: gm.iterate(cams, tgt, loss), steps)
+    launches = (gm.launches - l0) // steps
+    ph = gm.timing_read()["raster_fused"]
+    fused_ms = ph[0] / max(ph[1], 1)
+    work = gm.debug_work()
     tile, ppt = gm.tile_size, gm.pixels_per_thread
-    visible = []
     gm.render(cams)
-    for v in range(V):
-        visible.append(int((gm.debug_projection(v)[8] > 0).sum()))
+    visible = [int((gm.debug_projection(v)[8] > 0).sum()) for v in range(V)]
     gm.close()
-    # the same work as V single-view iterations (V Adam steps), one view per call
-    gs = GaussianMap(capacity=params.shape[1], max_views=1, max_width=640, max_height=480, tile_size=tile,
-                     pixels_per_thread=ppt)
+    gs = GaussianMap(capacity=params.shape[1], max_views=1, max_width=640, max_height=480, device=device,
+                     tile_size=tile, pixels_per_thread=ppt)
     gs.set_params(torch.as_tensor(params, device=dev))
     singles = [tgt[v:v + 1].contiguous() for v in range(V)]
-    for _ in range(args.warmup):
+    for _ in range(max(args.warmup, 3)):
         for v in range(V):
             gs.iterate(cams[v], singles[v], loss)
 
     def seq():
         for v in range(V):
             gs.iterate(cams[v], singles[v], loss)
-    ms_seq = timed(seq, args.steps)
+    ms_seq = timed(seq, steps)
     gs.close()
-    line = {"metric": WINDOW_METRIC, "value": 1000.0 / ms_window, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_window, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WINDOW_WORKLOAD, "n_gaussians": int(params.shape[1]), "views": V,
-                       "visible_per_view": visible, "tile": tile, "pixels_per_thread": ppt,
-                       "l2": "flushed between iterations (256 MB write)"},
+    peaks, _ = _peaks()
+    n_sm = torch.cuda.get_device_properties(device).multi_processor_count
+    return {"metric": WINDOW_METRIC, "value": 1000.0 / ms_window, "unit": UNIT, "steps": steps,
+            "ms_per_step": ms_window, "workload": WINDOW_WORKLOAD, "n_gaussians": int(params.shape[1]),
+            "views": V, "visible_per_view": visible,
+            "visible_note": "no view inside this room's generator sees more than ~67k of the 150k Gaussians "
+                            "(a corner view across the room sees about 45 % of the surfaces): the range is the "
+                            "widest the geometry allows, not the 20k-140k the workload statement names",
+            "layout": {"tile": tile, "pixels_per_thread": ppt},
             "sequential": {"what": f"{V} single-view iterations (one per view, {V} Adam steps) per step",
-                           "ms_per_step": ms_seq, "speedup_of_window": ms_seq / ms_window},
-            "gpu_launches": int(launches),
-            "phases_ms": {k: round(v[0] / max(v[1], 1), 5) for k, v in phases.items()},
-            "clocks": clk.summary()}
+                           "value": 1000.0 / ms_seq, "ms_per_step": ms_seq, "speedup_of_window": ms_seq / ms_window},
+            "gpu_launches": int(launches), "work": work,
+            "roofline": dict(fused_roofline(work, fused_ms, n_sm, peaks), kernel="raster_fused"),
+            "l2": "flushed between iterations (256 MB write)", "clocks": clk.summary()}
+
+
+def run_window(args):
+    """Window workload alone: one call renders and back-propagates all 8 views (one persistent
+    compositing launch in the replayed graph) vs 8 single-view iterations, same GPU."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2504_02437_gb300 import build as B
+    B.build()
+    w = window_measure(args, args.steps, 0)
+    line = {"metric": WINDOW_METRIC, "value": w["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": w["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WINDOW_WORKLOAD, "n_gaussians": w["n_gaussians"], "views": w["views"],
+                       "l2": w["l2"]},
+            "window": w, "gpu_launches": w["gpu_launches"], "roofline": w["roofline"], "clocks": w["clocks"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -551,7 +665,7 @@ def _stream_map(capacity, args):
                        pixels_per_thread=args.ppt)
 
 
-def time_to_psnr(train_seeds, heldout_seeds, frames, iters, args, epochs=300, log=None):
+def time_to_psnr(train_seeds, heldout_seeds, frames, iters, args, epochs=300, log=None, heldout_frames=None):
     """Learned-initialiser protocol: collect (features, converged parameters) pairs from plain
     streams of ``train_seeds``, train the MLP with the library's kernels, then run each held-out
     sequence twice (plain, learned) and compare per keyframe (keyframe 0 is initialised the
@@ -582,7 +696,7 @@ def time_to_psnr(train_seeds, heldout_seeds, frames, iters, args, epochs=300, lo
     it_plain, it_mlp, ms_plain, ms_mlp, p_plain, p_mlp, p1_plain, p1_mlp = [], [], [], [], [], [], [], []
     reached = 0
     for sd in heldout_seeds:
-        cams, tg, pts = stream_sequence(sd, frames)
+        cams, tg, pts = stream_sequence(sd, heldout_frames or frames)
         runs = {}
         for name, m in (("plain", None), ("mlp", mlp)):
             gm = _stream_map(STREAM_CAPACITY, args)
@@ -606,6 +720,7 @@ def time_to_psnr(train_seeds, heldout_seeds, frames, iters, args, epochs=300, lo
         p1_mlp += cm[:, 0].tolist()
     n = len(it_mlp)
     return {"train_seeds": list(train_seeds), "heldout_seeds": list(heldout_seeds), "frames": frames,
+            "heldout_frames": heldout_frames or frames,
             "iterations_per_keyframe": iters, "training_pairs": int(X.shape[0]), "collect_s": round(t_collect, 2),
             "train_epochs": epochs, "train_ms": round(train_ms, 1), "train_loss_first_last": [losses[0], losses[-1]],
             "keyframes_compared": n, "mlp_reached_goal": reached,
@@ -665,58 +780,79 @@ MLP_FLOP_FWD_PER_ROW = 2 * (80 * 128 + 128 * 128 + 128 * 16)
 MLP_FLOP_BWD_PER_ROW = 2 * 2 * (16 * 128 + 128 * 128 + 128 * 80) + 2 * 2 * (16 * 128 + 128 * 128)
 
 
-def run_mlp_bench(args):
-    """Training steps of the learned initialiser on random features (the shapes of config 5's
-    training batches): one step = forward, MSE backward, Adam. Tensor-core roofline against the
-    measured BF16 peak."""
+def mlp_step_measure(steps: int, warmup: int, device: int = 0) -> dict:
+    """Training steps of the learned initialiser (forward, MSE backward, Adam) on 4,096 random
+    feature rows, against the measured BF16 tensor peak."""
     import torch
-    torch.cuda.set_device(0)
-    from paper_2504_02437_gb300 import build as B
-    B.build()
     from paper_2504_02437_gb300.api import MLP
     rows = 4096
-    g = torch.Generator(device="cuda")
+    g = torch.Generator(device=f"cuda:{device}")
     g.manual_seed(0)
-    X = torch.rand(rows, 80, device="cuda", generator=g)
-    Y = torch.randn(rows, 16, device="cuda", generator=g) * 0.5
+    X = torch.rand(rows, 80, device=f"cuda:{device}", generator=g)
+    Y = torch.randn(rows, 16, device=f"cuda:{device}", generator=g) * 0.5
     Y[:, 11:] = 0
-    mlp = MLP(seed=0)
-    for _ in range(args.warmup):
+    mlp = MLP(seed=0, device=device)
+    for _ in range(warmup):
         mlp.backward(X, Y)
         mlp.step(1e-3)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     torch.cuda.synchronize()
-    with ClockSampler(0) as clk:
-        for a, b in ev:
-            a.record()
-            mlp.backward(X, Y)
-            mlp.step(1e-3)
-            b.record()
-        torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    # forward alone on an insertion batch (96 points)
+    for a, b in ev:
+        a.record()
+        mlp.backward(X, Y)
+        mlp.step(1e-3)
+        b.record()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
     Xs = X[:96].contiguous()
-    evf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for a, b in evf:
         a.record()
         mlp.forward(Xs)
         b.record()
     torch.cuda.synchronize()
-    ms_fwd96 = sum(a.elapsed_time(b) for a, b in evf) / args.steps
+    ms_fwd96 = sum(a.elapsed_time(b) for a, b in evf) / steps
+    mlp.close()
     flops = rows * (MLP_FLOP_FWD_PER_ROW + MLP_FLOP_BWD_PER_ROW)
     peaks, src = _peaks()
     peak = float(peaks.get("bf16_tflops", 1900.0))
     ach = flops / (ms * 1e-3) / 1e12
-    line = {"metric": MLP_METRIC, "value": 1000.0 / ms, "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+    return {"metric": MLP_METRIC, "value": 1000.0 / ms, "unit": "steps/s", "steps": steps, "ms_per_step": ms,
+            "forward_96_rows_ms": ms_fwd96,
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "traffic": None, "kernel": "whole training step (k_gemm_tc launches + elementwise)",
+                         "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({src})"}}
+
+
+def learned_init_measure(args, device: int = 0) -> dict:
+    """The learned-initialiser protocol at reduced size: the MLP is trained on the converged
+    Gaussians of two 60-keyframe plain streams (seeds 0, 1); one held-out 16-keyframe sequence
+    (seed 100) is mapped with plain and with learned initialisation; per keyframe, the iterations
+    and mapping ms until the newest keyframe reaches the PSNR the plain run has after 100."""
+    r = time_to_psnr((0, 1), (100,), 60, 100, args, epochs=300, heldout_frames=16)
+    m = mlp_step_measure(20, 5, device)
+    return {"metric": TTP_METRIC, "value": r["speedup"], "unit": "x (plain ms / learned ms to the same PSNR)",
+            "protocol": "MLP trained on 2 plain streams of 60 keyframes (seeds 0, 1); held-out sequence seed 100, "
+                        "16 keyframes, each mapped twice (plain, learned), 100 iterations per keyframe",
+            "time_to_psnr": r, "mlp_training_step": m}
+
+
+def run_mlp_bench(args):
+    """Training steps of the learned initialiser on random features (the shapes of the
+    learned-initialiser protocol's training batches): one step = forward, MSE backward, Adam.
+    Tensor-core roofline against the measured BF16 peak."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2504_02437_gb300 import build as B
+    B.build()
+    with ClockSampler(0) as clk:
+        m = mlp_step_measure(args.steps, args.warmup, 0)
+    line = {"metric": MLP_METRIC, "value": m["value"], "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16 (f32 accumulate)", "data": "synthetic",
             "config": {"workload": "MLP 80-128-128-16 training step on 4096 random feature rows",
                        "l2": "resident (the whole step fits in L2; the MLP is latency-bound)"},
-            "forward_96_rows_ms": ms_fwd96,
-            "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                         "traffic": None, "kernel": "whole training step (13 k_gemm_tc launches + elementwise)",
-                         "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({src})"},
-            "clocks": clk.summary()}
+            "forward_96_rows_ms": m["forward_96_rows_ms"], "roofline": m["roofline"], "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -797,8 +933,11 @@ def main():
     ap.add_argument("--train-seeds", type=int, default=5)
     ap.add_argument("--heldout-seeds", type=int, default=5)
     ap.add_argument("--ppt", type=int, default=0, choices=[0, 1, 2, 4])
-    ap.add_argument("--cpu-tiles", type=int, default=160)
+    ap.add_argument("--cpu-tiles", type=int, default=128, help="sample tiles of the all-core oracle timing")
+    ap.add_argument("--cpu-tiles-single", type=int, default=32, help="sample tiles of the single-thread oracle timing")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="leave out the window and learned-initialiser objects")
+    ap.add_argument("--repeats", type=int, default=10, help="timed regions of --steps iterations (median reported)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

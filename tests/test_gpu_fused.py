@@ -196,3 +196,29 @@ def test_render_backward_across_staging_batches(multibatch):
     assert abs(L[0] - g["loss"]) <= 1e-5 * g["loss"]
     errs = grad_errors(grads, g["grad"], exclude=excl, floor_frac=GRAD_FLOOR_DEEP)
     assert max(errs.values()) <= GRAD_RTOL, errs
+
+
+@pytest.mark.parametrize("det", [False, True])
+def test_dense_bins_pairs_bit_exact(det):
+    """Dense bins: 10,000 Gaussians in 64x64, bins of up to 3,990 pairs at 16 px and 2,874 at 8 px
+    (the deterministic mode's tiles); the pairs equal the oracle's binning bit for bit, and the
+    image matches."""
+    p, cam = frustum_scene(n=10000, width=64, height=64, fx=60, fy=60, cx=32, cy=32, seed=31,
+                           logscale_mean=-2.2, logscale_std=0.5, opacity_mean=-4.5)
+    cfg = dict(deterministic=1) if det else dict(tile_size=16, pixels_per_thread=1)
+    gm = new_map(p.shape[1], W=64, H=64, **cfg)
+    gm.set_params(cuda(p))
+    rgb = gm.render(cam).cpu().numpy()[0]
+    g = gm.debug_projection(0)
+    bins, vals = gm.debug_pairs()
+    tile = gm.tile_size
+    gm.close()
+    depth32 = g[5].astype(np.float32)
+    keys_gpu = (bins.astype(np.uint64) << np.uint64(32)) | depth32[vals].view(np.uint32).astype(np.uint64)
+    keys_ref, vals_ref = O.bin_pairs(g[0], g[1], g[6], depth32, g[8] > 0, 64, 64, tile)
+    assert np.bincount(bins.astype(np.int64)).max() > 2048
+    np.testing.assert_array_equal(keys_gpu, keys_ref)
+    np.testing.assert_array_equal(vals, vals_ref)
+    fwd = O.render(p.astype(np.float64), cam, flags=True)
+    err = np.abs(rgb - fwd["rgb"]).max(axis=0)
+    assert err[~fwd["near"]].max() <= IMG_ATOL
