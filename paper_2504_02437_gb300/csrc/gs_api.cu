@@ -1012,16 +1012,17 @@ int gs_debug_grad2d(gs_ctx* c, float* out) {
         free(g);
         return fail(c, GS_ERR_CUDA, "debug copy", e);
     }
-    const float k1 = -0.5f * kLog2e, k2 = -kLog2e;
+    // the records hold the first five values without the factor ln 2 of d 2^p / dp; the exp2
+    // scaling of the conic (a' = -a log2(e) / 2, b' = -b log2(e)) cancels it for a, b, c
     for (int v = 0; v < c->n_views; ++v)
         for (size_t i = 0; i < n; ++i) {
             const float* r = g + (v * n + i) * kGrad2dStride;
             float* o = out + (size_t)v * 9 * n;
-            o[0 * n + i] = r[0];
-            o[1 * n + i] = r[1];
-            o[2 * n + i] = r[2] * k1;
-            o[3 * n + i] = r[3] * k2;
-            o[4 * n + i] = r[4] * k1;
+            o[0 * n + i] = r[0] * kLn2;
+            o[1 * n + i] = r[1] * kLn2;
+            o[2 * n + i] = r[2] * -0.5f;
+            o[3 * n + i] = -r[3];
+            o[4 * n + i] = r[4] * -0.5f;
             o[5 * n + i] = r[5];
             o[6 * n + i] = r[6];
             o[7 * n + i] = r[7];

@@ -287,7 +287,6 @@ __global__ void __launch_bounds__(128) k_preprocess_backward(
     Shape g;
     shape_of(p, g);
     Proj o;
-    const float k1 = -0.5f * kLog2e, k2 = -kLog2e;
     for (int view = 0; view < n_views; ++view) {
         size_t item = (size_t)view * n + gid;
         if (tiles[item] == 0) continue;
@@ -295,8 +294,10 @@ __global__ void __launch_bounds__(128) k_preprocess_backward(
         const float4 g0 = *reinterpret_cast<const float4*>(grad2d + item * kGrad2dStride);
         const float4 g1 = *reinterpret_cast<const float4*>(grad2d + item * kGrad2dStride + 4);
         const float g8 = grad2d[item * kGrad2dStride + 8];
-        float gu = g0.x, gv = g0.y;
-        float ga = g0.z * k1, gb = g0.w * k2, gc = g1.x * k1;   // to the unscaled conic
+        // the compositing adjoint leaves out the factor ln 2 of the first five values; with the
+        // exp2 scaling of the conic (a' = -a log2(e) / 2, b' = -b log2(e)) it cancels there
+        float gu = g0.x * kLn2, gv = g0.y * kLn2;
+        float ga = -0.5f * g0.z, gb = -g0.w, gc = -0.5f * g1.x;   // to the unscaled conic
         dop += g1.y;
         dr += g1.z;
         dg += g1.w;

@@ -123,13 +123,13 @@ struct Layout {
     }
 };
 
-// Base-2 exponent a' dx^2 + b' dx dy + c' dy^2 of a Gaussian at a pixel,
-// written with explicit rounding so that every kernel takes bit-identical
-// decisions; the column part (a' dx and b' dx) is shared by a thread's pixels.
-__device__ __forceinline__ float power2_split(float qxdx, float qydx, float qz, float dx, float dy) {
-    float t = __fmul_rn(__fmul_rn(qz, dy), dy);
-    t = __fmaf_rn(qydx, dy, t);
-    return __fmaf_rn(qxdx, dx, t);
+// Base-2 exponent a' dx^2 + b' dx dy + c' dy^2 of a Gaussian at a pixel, as a
+// polynomial in dy: (c' dy + b' dx) dy + a' dx^2, with the column terms
+// b' dx and a' dx^2 formed once per (thread, Gaussian) and shared by the
+// thread's pixels; two fused multiply-adds per pixel. Written with explicit
+// rounding so that every kernel takes bit-identical decisions.
+__device__ __forceinline__ float power2_dy(float qz, float qydx, float qxdx2, float dy) {
+    return __fmaf_rn(__fmaf_rn(qz, dy, qydx), dy, qxdx2);
 }
 
 // Warp sum of 9 values by recursive halving: at each step a lane keeps half of
@@ -313,7 +313,7 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
             if (fabsf(dx) > a.z) continue;
             const float4 q = s1[k];
             const float thr = s2[k].w;
-            const float qxdx = __fmul_rn(q.x, dx), qydx = __fmul_rn(q.y, dx);
+            const float qydx = __fmul_rn(q.y, dx), qxdx2 = __fmul_rn(__fmul_rn(q.x, dx), dx);
             // exponent and membership of every pixel first, without branches, so the
             // pixels' dependent chains interleave (5 % on the 300k-Gaussian keyframe
             // together with the same split in the adjoint)
@@ -323,7 +323,7 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
 #pragma unroll
             for (int p = 0; p < PPT; ++p) {
                 const float dy = fy[p] - a.y;
-                p2v[p] = power2_split(qxdx, qydx, q.z, dx, dy);
+                p2v[p] = power2_dy(q.z, qydx, qxdx2, dy);
                 hit[p] = live[p] && fabsf(dy) <= a.w && p2v[p] >= thr;
                 any_hit |= hit[p];
             }
@@ -357,7 +357,8 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
 // Adjoint of the compositing for a thread's PPT pixels: walks the tile's list
 // back to front from the block's largest last-blended entry, recovering
 // T_i = T_{i+1} / (1 - alpha_i) from the final T, and accumulates the
-// gradients w.r.t. each Gaussian's screen quantities (when at most
+// gradients w.r.t. each Gaussian's screen quantities (the first five, u, v and
+// the exp2-scaled conic a', b', c', without the factor ln 2 of d 2^p / dp) (when at most
 // kLaneAtomicMax lanes blended it, each adds its own 9 values with two float4
 // atomics and one scalar; else a warp sum, then one 9-lane atomic). Each
 // warp visits only the batch entries its compacted list holds, which stop at
@@ -378,13 +379,13 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
     __shared__ uint32_t smax;
     const int lane = threadIdx.x & 31;
     const uint2 rg = g.rg;
-    float fy[PPT], ar[PPT], ag[PPT], ab[PPT];
+    float fy[PPT], ga[PPT];   // ga: upstream gradient . normalised colour behind the current Gaussian
     uint32_t my_end[PPT];
     uint32_t thread_end = rg.x;
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
         fy[p] = (float)g.py(p) - g.oy;
-        ar[p] = ag[p] = ab[p] = 0.f;
+        ga[p] = 0.f;
         my_end[p] = rg.x + cnt_last[p];
         thread_end = max(thread_end, my_end[p]);
     }
@@ -427,13 +428,13 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
             if (col) {
                 const float4 q = s1[k];
                 const float4 c = s2[k];
-                const float qxdx = __fmul_rn(q.x, dx), qydx = __fmul_rn(q.y, dx);
+                const float qydx = __fmul_rn(q.y, dx), qxdx2 = __fmul_rn(__fmul_rn(q.x, dx), dx);
                 float p2v[PPT];
                 bool hit[PPT];
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {   // as in the forward: all pixels' tests first
                     const float dy = fy[p] - a.y;
-                    p2v[p] = power2_split(qxdx, qydx, q.z, dx, dy);
+                    p2v[p] = power2_dy(q.z, qydx, qxdx2, dy);
                     hit[p] = pos < my_end[p] && fabsf(dy) <= a.w && p2v[p] >= c.w;
                 }
                 float Gv[PPT];   // all pixels' ex2 back to back (the MUFU pipe has room)
@@ -453,20 +454,21 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
                     acc[6] = fmaf(gr[p], wgt, acc[6]);
                     acc[7] = fmaf(gg[p], wgt, acc[7]);
                     acc[8] = fmaf(gb[p], wgt, acc[8]);
-                    const float dalpha = T[p] * (gr[p] * (c.x - ar[p]) + gg[p] * (c.y - ag[p]) + gb[p] * (c.z - ab[p]));
-                    ar[p] = fmaf(alpha, c.x - ar[p], ar[p]);
-                    ag[p] = fmaf(alpha, c.y - ag[p], ag[p]);
-                    ab[p] = fmaf(alpha, c.z - ab[p], ab[p]);
-                    if (oG <= kc.alpha_max) {
-                        // dL/dp2 with alpha = o 2^p2
-                        const float g2 = dalpha * oG * kLn2;
-                        acc[0] -= g2 * (2.f * q.x * dx + q.y * dy);
-                        acc[1] -= g2 * (q.y * dx + 2.f * q.z * dy);
-                        acc[2] = fmaf(g2 * dx, dx, acc[2]);
-                        acc[3] = fmaf(g2 * dx, dy, acc[3]);
-                        acc[4] = fmaf(g2 * dy, dy, acc[4]);
-                        acc[5] = fmaf(dalpha, G, acc[5]);
-                    }
+                    // dL/dalpha = T (g . c - g . a), with a the normalised colour behind this
+                    // Gaussian, a <- a + alpha (c - a); g is fixed per pixel, so only g . a is kept
+                    const float d = fmaf(gr[p], c.x, fmaf(gg[p], c.y, gb[p] * c.z)) - ga[p];
+                    const float dalpha = T[p] * d;
+                    ga[p] = fmaf(alpha, d, ga[p]);
+                    // through alpha = o 2^p2, zero where the 0.99 clamp holds; the factor ln 2
+                    // of d(2^p2)/dp2 is left to the readers of the screen gradients
+                    const bool open = oG <= kc.alpha_max;
+                    const float g2 = open ? dalpha * oG : 0.f;
+                    acc[0] -= g2 * (2.f * q.x * dx + q.y * dy);
+                    acc[1] -= g2 * (q.y * dx + 2.f * q.z * dy);
+                    acc[2] = fmaf(g2 * dx, dx, acc[2]);
+                    acc[3] = fmaf(g2 * dx, dy, acc[3]);
+                    acc[4] = fmaf(g2 * dy, dy, acc[4]);
+                    acc[5] = fmaf(dalpha, open ? G : 0.f, acc[5]);
                 }
             }
             const uint32_t who = __ballot_sync(0xFFFFFFFFu, any);
@@ -686,7 +688,7 @@ __global__ void __launch_bounds__(TILE* TILE) k_count_work(const uint2* __restri
         ++tested;
         const float dx = fx - a.x, dy = fy - a.y;
         if (fabsf(dx) > a.z || fabsf(dy) > a.w) continue;
-        const float p2 = power2_split(__fmul_rn(q.x, dx), __fmul_rn(q.y, dx), q.z, dx, dy);
+        const float p2 = power2_dy(q.z, __fmul_rn(q.y, dx), __fmul_rn(__fmul_rn(q.x, dx), dx), dy);
         if (p2 < c.w) continue;
         const float alpha = fminf(kc.alpha_max, __fmul_rn(q.w, ex2_approx(p2)));
         const float Tn = __fmul_rn(T, 1.f - alpha);

@@ -12,17 +12,18 @@ IMG_ATOL = 1e-4          # max abs pixel error
 GRAD_RTOL = 1e-3         # per-parameter relative gradient error ...
 # ... relative to max(|g*|, GRAD_FLOOR * max |g*| of the parameter group). A gradient is a sum of
 # per-pixel terms that partly cancel; in FP32 its absolute error is ~eps32 times the sum of the
-# terms' magnitudes. Measured on the parity scenes (every compositing layout, the deterministic
-# mode, single and multi-view): |g - g*| <= 1.8e-6 of the group's largest gradient, and the
-# smallest floor under which every gradient passes is 7.4e-5 of it; GRAD_FLOOR keeps a margin
-# of 2.7 over that. The deep-list scene (pixels blending several hundred Gaussians) sums
-# correspondingly more terms: it needs 4.4e-4, and GRAD_FLOOR_DEEP keeps a margin of 2.3.
-GRAD_FLOOR = 2e-4
+# terms' magnitudes. Measured on the parity scenes (every compositing layout and the
+# deterministic mode): |g - g*| <= 2.3e-6 of the group's largest gradient; the smallest floor
+# under which every gradient passes is 5.4e-5 of it for single views and 2.0e-4 for the
+# three-view window (a Gaussian's views add terms that cancel); GRAD_FLOOR keeps a margin of
+# 2.5 over the window. The deep-list scene (pixels blending several hundred Gaussians) sums
+# correspondingly more terms: it needs 4.3e-4, and GRAD_FLOOR_DEEP keeps a margin of 2.3.
+GRAD_FLOOR = 5e-4
 GRAD_FLOOR_DEEP = 1e-3
-# Screen-space gradients of one view (du, dv, conic, opacity, colour per Gaussian) are sums over
-# fewer, more strongly cancelling pixel terms than the parameter gradients (which add all views
-# and the projection's chain): one rotated view of the three-view window needs 2.4e-4 of the
-# group's largest gradient; SCREEN_GRAD_FLOOR keeps a margin of 4.
+# One view's screen-space gradients (du, dv, conic, opacity, colour per Gaussian) sum fewer,
+# more strongly cancelling pixel terms; their measured need varies with the rounding order of
+# the compositing arithmetic (up to 2.4e-4 of the group's largest gradient over the kernel
+# versions measured), so SCREEN_GRAD_FLOOR keeps a margin of 4 over that.
 SCREEN_GRAD_FLOOR = 1e-3
 GROUPS = {"mean": slice(0, 3), "logscale": slice(3, 6), "quat": slice(6, 10), "opacity": slice(10, 11),
           "rgb": slice(11, 14)}

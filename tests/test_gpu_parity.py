@@ -6,7 +6,7 @@ compared bit-exactly (the oracle's binning is fed the kernel's FP32 screen
 quantities); images within 1e-4 absolute away from pixels where a discrete
 decision lies within FP32 rounding of its threshold; gradients within 1e-3
 relative, floored at a fraction of the group's largest gradient set from the
-measured FP32 accumulation error of these cancelling sums (2e-4 for parameter
+measured FP32 accumulation error of these cancelling sums (5e-4 for parameter
 gradients, 1e-3 for one view's screen-space gradients; tests/gpu_helpers.py).
 """
 import numpy as np
