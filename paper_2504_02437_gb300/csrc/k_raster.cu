@@ -273,14 +273,15 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
     float4* s1 = st.s1;
     float4* s2 = st.s2;
     uint32_t* sid = st.sid;
+    // a pixel that is outside the image or has stopped gets a row offset so far away that it
+    // fails every box test (and its exponent is -inf): no separate per-pixel flag to test
+    constexpr float kGone = 3.0e38f;
     float fy[PPT], wmax[PPT];
-    bool live[PPT];
     int nlive = 0;
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
-        fy[p] = (float)g.py(p) - g.oy;
-        live[p] = inside[p];
-        nlive += live[p] ? 1 : 0;
+        fy[p] = inside[p] ? (float)g.py(p) - g.oy : kGone;
+        nlive += inside[p] ? 1 : 0;
         T[p] = 1.f;
         cr[p] = cg[p] = cb[p] = 0.f;
         last[p] = 0;
@@ -324,7 +325,7 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
             for (int p = 0; p < PPT; ++p) {
                 const float dy = fy[p] - a.y;
                 p2v[p] = power2_dy(q.z, qydx, qxdx2, dy);
-                hit[p] = live[p] && fabsf(dy) <= a.w && p2v[p] >= thr;
+                hit[p] = fabsf(dy) <= a.w && p2v[p] >= thr;
                 any_hit |= hit[p];
             }
             if (!any_hit) continue;
@@ -334,7 +335,7 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
                 const float alpha = fminf(kc.alpha_max, __fmul_rn(q.w, ex2_approx(p2v[p])));
                 const float Tn = __fmul_rn(T[p], 1.f - alpha);
                 if (Tn < kc.T_min) {
-                    live[p] = false;
+                    fy[p] = kGone;
                     --nlive;
                     continue;
                 }
