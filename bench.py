@@ -47,7 +47,7 @@ FP32_LANES_PER_SM = 128
 # workload, with the kernel source's sha256 and layout at capture time (the figure is reported
 # only while both still match): profiles/raster_fused_replica_1200x680_300k.md
 NCU_TRAFFIC = {"raster_fused": {"bytes": 35.94e6, "source": "paper_2504_02437_gb300/csrc/k_raster.cu",
-                                "sha256": "69e7d039fabc38381fdc41fb42b1debad7d6f67316d7459ddccc20aa56ae1edd",
+                                "sha256": "61f95ef1ad05b23737e1c05dd44678b364949478be7b12b031d9ac1517025edb",
                                 "tile": 16, "ppt": 2}}
 
 
