@@ -112,3 +112,31 @@ def test_psnr_and_training_targets_match_oracle():
     with pytest.raises(GSError):
         gm.mlp_targets(2990, 20)
     gm.close()
+
+
+def test_ablation_switches_change_the_outcome():
+    """The switches of the paper's ablation (Table 4: insertion rule, densification, planar term)
+    on a short quarter-size stream: without densification the map stays small and renders the
+    newest keyframes worse; the planar term changes the trajectory but not the map's size much;
+    the distance rule of Eq. 7 inserts a different set of points than the opacity gate."""
+    from paper_2504_02437_gb300 import stream as S
+    from paper_2504_02437_gb300.api import GaussianMap
+    cams, tg, pts = stream_sequence(0, 12, W, H, FX)
+
+    def run(densify=True, **cfg):
+        gm = GaussianMap(capacity=400_000, max_views=8, max_width=W, max_height=H, **cfg)
+        st = S.run_stream(gm, cams, tg, pts, iters=60, track_psnr="final", densify=densify)
+        p = gm.params()
+        gm.close()
+        return st, p
+    full, p_full = run()
+    nodens, _ = run(densify=False)
+    noplanar, p_noplanar = run(lambda_reg=0.0)
+    dist, _ = run(insert_tau=0.05)
+    last = lambda st: float(st["psnr"][-4:].mean())  # noqa: E731
+    assert full["n_gauss"][-1] > 2 * nodens["n_gauss"][-1]
+    assert last(full) > last(nodens) + 1.0, (last(full), last(nodens))
+    assert np.isfinite(last(noplanar)) and abs(last(noplanar) - last(full)) < 3.0
+    assert not torch.equal(p_full[:, :100], p_noplanar[:, :100])
+    assert dist["n_inserted"] != full["n_inserted"]
+    assert np.isfinite(last(dist))
