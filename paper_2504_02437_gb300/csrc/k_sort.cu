@@ -154,7 +154,9 @@ __global__ void __launch_bounds__(256) k_digit_scan(uint32_t* __restrict__ hist,
 // histogram. The ranked round is first regrouped by digit in shared memory,
 // then written out by consecutive threads, so each digit's run of the round
 // leaves in coalesced stores instead of one scattered store per element.
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+// Five CTAs per SM (at most 51 registers; A/B on the 300k-Gaussian keyframe: iteration
+// 0.5494 -> 0.5467 ms).
+__global__ void __launch_bounds__(kSortThreads, 5) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* __restrict__ n_dev, uint32_t n_max, int shift, int nbits,
     const uint32_t* __restrict__ hist, const uint32_t* __restrict__ dtot) {
