@@ -139,7 +139,7 @@ def make_workload(seed: int = 0):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms during a timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -153,7 +153,7 @@ class ClockSampler:
         try:
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -953,7 +953,7 @@ def main():
     ap.add_argument("--cpu-tiles-single", type=int, default=32, help="sample tiles of the single-thread oracle timing")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="leave out the window and learned-initialiser objects")
-    ap.add_argument("--repeats", type=int, default=10, help="timed regions of --steps iterations (median reported)")
+    ap.add_argument("--repeats", type=int, default=30, help="timed regions of --steps iterations (median reported)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -306,6 +306,10 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
         const int nk = build_warp_list(st, cnt, 0u, 0xFFFFFFFFu);
         const typename Stage<kBatch, NT / 32>::Idx* wl = st.list[threadIdx.x >> 5];
         int knext = nk > 0 ? (int)wl[0] : 0;   // the next entry's index is loaded one visit ahead
+        // unrolled by two: the next entry's record loads and membership tests interleave with
+        // this entry's blending (A/B on the 300k-Gaussian keyframe, 16 x 2 layout: fused kernel
+        // 0.380 -> 0.362 ms; the other layouts and the window unchanged; by four no better)
+#pragma unroll 2
         for (int i = 0; i < nk && nlive > 0; ++i) {
             const int k = knext;
             if (i + 1 < nk) knext = wl[i + 1];
