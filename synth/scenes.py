@@ -275,15 +275,25 @@ def make_room(seed: int = 0, half=(3.0, 1.5, 3.0), n_boxes: int = 20) -> Room:
 
 
 def room_gaussians(room: Room, n: int, seed: int = 0, logscale_mean: float = -4.0,
-                   logscale_std: float = 0.5, opacity_mean: float = 1.0, opacity_std: float = 1.0):
+                   logscale_std: float = 0.5, opacity_mean: float = 1.0, opacity_std: float = 1.0,
+                   box_fraction=None):
     """``n`` Gaussians sampled area-uniformly on the room's rectangles, coloured by the texture.
 
-    Log-scales ~ N(logscale_mean, logscale_std); opacity logits ~ N(opacity_mean, opacity_std);
-    quaternions normalised N(0, I4). Returns params [14, n] float32.
+    With ``box_fraction`` that share of the Gaussians goes to the boxes' faces and the rest to
+    the six walls, area-uniformly within each group (a map denser on the objects than on the
+    walls). Log-scales ~ N(logscale_mean, logscale_std); opacity logits ~ N(opacity_mean,
+    opacity_std); quaternions normalised N(0, I4). Returns params [14, n] float32.
     """
     rng = _rng(20_000 + seed)
     areas = room.areas()
-    k = rng.choice(room.n_rects, size=n, p=areas / areas.sum())
+    w = areas / areas.sum()
+    if box_fraction is not None:
+        wall = np.arange(room.n_rects) < 6
+        w = areas.copy()
+        w[wall] *= (1.0 - box_fraction) / areas[wall].sum()
+        w[~wall] *= box_fraction / areas[~wall].sum()
+        w = w / w.sum()
+    k = rng.choice(room.n_rects, size=n, p=w)
     a = rng.uniform(0.0, 1.0, size=n) * room.ext[k, 0]
     b = rng.uniform(0.0, 1.0, size=n) * room.ext[k, 1]
     mean = room.origin[k] + a[:, None] * room.e1[k] + b[:, None] * room.e2[k]
