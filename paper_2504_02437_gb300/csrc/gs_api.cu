@@ -249,6 +249,22 @@ struct Phase {
     }
 };
 
+// The zeroing a mapping iteration needs before its pair emission (overflow flag, bin ranges)
+// and before its adjoint (screen gradients), issued on the side stream at the iteration's start
+// so that it runs beside the projection and the depth sort; back_half and iteration_tail wait
+// for it instead of zeroing on the main stream.
+int side_begin(gs_ctx* c, cudaStream_t s) {
+    CK(cudaEventRecord(c->side_ev[0], s));
+    CK(cudaStreamWaitEvent(c->side, c->side_ev[0], 0));
+    CK(cudaMemsetAsync(c->dcount + 1, 0, sizeof(uint32_t), c->side));
+    CK(cudaMemsetAsync(c->ranges, 0, sizeof(uint2) * (size_t)c->n_bins, c->side));
+    CK(cudaEventRecord(c->side_ev[1], c->side));
+    CK(cudaMemsetAsync(c->grad2d, 0, sizeof(float) * kGrad2dStride * c->n_views * (size_t)c->n, c->side));
+    CK(cudaEventRecord(c->side_ev[2], c->side));
+    c->side_zeroed = true;
+    return GS_OK;
+}
+
 // Projection, depth sort, scan. Leaves P in dcount[0].
 int front_half(gs_ctx* c, const DevConst& k, cudaStream_t s) {
     const uint32_t items = (uint32_t)c->n_views * (uint32_t)c->n;
@@ -267,7 +283,10 @@ int back_half(gs_ctx* c, const DevConst& k, float* rgb, int32_t* argmax, cudaStr
     const uint32_t items = (uint32_t)c->n_views * (uint32_t)c->n;
     {
         Phase ph(c, GS_PHASE_BIN, s);
-        CK(cudaMemsetAsync(c->dcount + 1, 0, sizeof(uint32_t), s));
+        if (c->side_zeroed)
+            CK(cudaStreamWaitEvent(s, c->side_ev[1], 0));   // overflow flag and ranges zeroed
+        else
+            CK(cudaMemsetAsync(c->dcount + 1, 0, sizeof(uint32_t), s));
         CK(emit_pairs(c, items, c->dcount + 8, s));
         int bits = std::max(1, ceil_log2((uint32_t)c->n_bins));
         CK(radix_sort_pairs(c, c->pkey, c->pval, c->dcount, (uint32_t)std::min<int64_t>(c->pair_cap, 0xFFFFFFFFll),
@@ -403,6 +422,9 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         ok = ok && cudaMallocHost((void**)&c->hcount, sizeof(uint32_t) * 16) == cudaSuccess;
         ok = ok && cudaMallocHost((void**)&c->hflags, sizeof(uint32_t) * 4) == cudaSuccess;
         ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+        ok = ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
+        for (int i = 0; i < 5; ++i)
+            ok = ok && cudaEventCreateWithFlags(&c->side_ev[i], cudaEventDisableTiming) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&c->graph_done, cudaEventDisableTiming) == cudaSuccess;
         if (!ok) { code = fail(c, GS_ERR_OOM, "device allocation failed"); break; }
         uint32_t init[16] = {0, 0, 0, 0xFFFFFFFFu, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -446,6 +468,9 @@ void gs_destroy(gs_ctx* c) {
     if (c->hcount) cudaFreeHost(c->hcount);
     if (c->hflags) cudaFreeHost(c->hflags);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side) cudaStreamDestroy(c->side);
+    for (int i = 0; i < 5; ++i)
+        if (c->side_ev[i]) cudaEventDestroy(c->side_ev[i]);
     if (c->graph_done) cudaEventDestroy(c->graph_done);
     delete c;
 }
@@ -610,21 +635,36 @@ static int iteration_tail(gs_ctx* c, const DevConst& k, const float* target, con
                 cudaSuccess)
             return fail(c, GS_ERR_CUDA, "loss launch", cudaGetLastError());
     }
-    CK(cudaMemsetAsync(c->grad2d, 0, sizeof(float) * kGrad2dStride * c->n_views * (size_t)c->n, s));
+    if (c->side_zeroed)
+        CK(cudaStreamWaitEvent(s, c->side_ev[2], 0));   // grad2d zeroed
+    else
+        CK(cudaMemsetAsync(c->grad2d, 0, sizeof(float) * kGrad2dStride * c->n_views * (size_t)c->n, s));
+    // the loss total (and, when capturing, the copy of the pair count and overflow flag) on the
+    // side stream, beside the projection adjoint and Adam
+    cudaStream_t ts = c->side_zeroed ? c->side : s;
     if (ssim) {
         Phase ph(c, GS_PHASE_RASTER_BWD, s);
         CK(launch_raster_backward(c, k, c->dLdC, s));
+        if (c->side_zeroed) {
+            CK(cudaEventRecord(c->side_ev[3], s));
+            CK(cudaStreamWaitEvent(ts, c->side_ev[3], 0));
+        }
     } else {
         int fgrid = 0;
         {
             Phase ph(c, GS_PHASE_RASTER_FUSED, s);
             CK(launch_raster_fused(c, k, target, slot, rgb, c->fpart, c->n_fpart, &fgrid, s));
         }
-        Phase ph(c, GS_PHASE_LOSS, s);
+        if (c->side_zeroed) {
+            CK(cudaEventRecord(c->side_ev[3], s));
+            CK(cudaStreamWaitEvent(ts, c->side_ev[3], 0));
+        }
+        Phase ph(c, GS_PHASE_LOSS, ts);
         // the deterministic mode sums the per-tile partials, the default the per-CTA ones
         const bool det = c->tile_part != nullptr;
-        CK(launch_loss_tail(c, k, det ? c->tile_part : c->fpart, det ? c->n_bins : fgrid, loss_out, s));
+        CK(launch_loss_tail(c, k, det ? c->tile_part : c->fpart, det ? c->n_bins : fgrid, loss_out, ts));
     }
+    if (capture) CK(cudaMemcpyAsync(c->hflags, c->dcount, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, ts));
     {
         Phase ph(c, GS_PHASE_PROJECT_BWD, s);
         CK(reduce_pair_grads(c, s));
@@ -634,7 +674,11 @@ static int iteration_tail(gs_ctx* c, const DevConst& k, const float* target, con
         Phase ph(c, GS_PHASE_ADAM, s);
         CK(launch_adam(c, s));
     }
-    if (capture) CK(cudaMemcpyAsync(c->hflags, c->dcount, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, s));
+    if (c->side_zeroed) {
+        CK(cudaEventRecord(c->side_ev[4], ts));
+        CK(cudaStreamWaitEvent(s, c->side_ev[4], 0));   // join: the iteration ends on s
+        c->side_zeroed = false;
+    }
     return GS_OK;
 }
 
@@ -789,6 +833,7 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
     ++c->launches;
     k_set_cams<<<1, 32, 0, s>>>(b, c->dcam, c->target_slot);
     CK(cudaGetLastError());
+    if ((code = side_begin(c, s)) != GS_OK) return code;
     if ((code = front_half(c, k, s)) != GS_OK) return code;
     CK(cudaMemcpyAsync(c->hcount, c->dcount, sizeof(uint32_t) * 9, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -802,7 +847,9 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
         if (want > c->pair_cap && alloc_pairs(c, want) != cudaSuccess)
             return fail(c, GS_ERR_OOM, "growing the pair buffers failed");
     }
-    if ((code = iteration_tail(c, k, target, c->target_slot, rgb, loss_out, false, s)) != GS_OK) return code;
+    code = iteration_tail(c, k, target, c->target_slot, rgb, loss_out, false, s);
+    c->side_zeroed = false;   // (also after an error part-way)
+    if (code != GS_OK) return code;
     c->adam_t += 1;
     c->rendered_rgb = rgb;
     const int64_t launches0 = c->launches;
@@ -818,12 +865,14 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
     {
         ++c->launches;
         k_set_cams<<<1, 32, 0, cs>>>(b, c->dcam, c->target_slot);
-        cc = front_half(c, k, cs);
+        cc = side_begin(c, cs);
+        if (cc == GS_OK) cc = front_half(c, k, cs);
         if (cc == GS_OK) cc = iteration_tail(c, k, target, c->target_slot, rgb, loss_out, true, cs);
     }
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(cs, &g);
     c->capturing = false;
+    c->side_zeroed = false;
     c->graph_kernels = c->launches - launches0;
     c->launches = launches0;
     if (cc != GS_OK || e != cudaSuccess || !g) {

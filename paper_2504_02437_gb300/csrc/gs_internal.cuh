@@ -144,6 +144,13 @@ struct gs_ctx {
     float* graph_loss = nullptr;
     float* graph_rgb = nullptr;
     cudaStream_t cap_stream = nullptr;      // stream the iteration is captured on
+    // second stream of a mapping iteration: the zeroing it needs later runs there from its start,
+    // overlapping the projection and the sorts, and the loss total runs there beside the
+    // projection adjoint and Adam (a fork and joins, which a captured graph keeps as branches)
+    cudaStream_t side = nullptr;
+    cudaEvent_t side_ev[5] = {};            // fork, overflow flag + ranges zeroed, grad2d zeroed,
+                                            // second fork, side work done
+    bool side_zeroed = false;               // this iteration's zeroing was issued on `side`
     cudaEvent_t graph_done = nullptr;       // recorded after each replay
     bool graph_pending = false;             // a replay's flags have not been checked yet
     uint32_t* hflags = nullptr;             // pinned: [0] pairs, [1] overflow of the last replay

@@ -550,7 +550,8 @@ cudaError_t reduce_pair_grads(gs_ctx* c, cudaStream_t s) {
 }
 
 cudaError_t compute_ranges(gs_ctx* c, cudaStream_t s) {
-    cudaMemsetAsync(c->ranges, 0, sizeof(uint2) * (size_t)c->n_bins, s);
+    // (a mapping iteration zeroes the ranges on its side stream)
+    if (!c->side_zeroed) cudaMemsetAsync(c->ranges, 0, sizeof(uint2) * (size_t)c->n_bins, s);
     ++c->launches;
     k_ranges<<<c->num_sms * 8, 256, 0, s>>>(c->pkey[c->pair_buf], c->dcount, (uint64_t)c->pair_cap,
                                             (uint32_t)c->n_bins, c->ranges);
