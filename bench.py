@@ -71,7 +71,9 @@ def _h2d_async():
     rt.cudaMemcpyAsync.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]
 
     def copy(dst, src, stream):
+        # a raw byte copy: both sides must be contiguous in the same element order
         assert src.is_pinned() and dst.is_cuda and dst.numel() == src.numel() and dst.dtype == src.dtype
+        assert src.is_contiguous() and dst.is_contiguous()
         err = rt.cudaMemcpyAsync(dst.data_ptr(), src.data_ptr(), src.numel() * src.element_size(), 1,
                                  stream.cuda_stream)
         if err != 0:
@@ -134,7 +136,7 @@ def make_workload(seed: int = 0):
     if os.path.exists(cache):
         target = np.load(cache)
     else:
-        target = room.raycast(cam)
+        target = np.ascontiguousarray(room.raycast(cam))
         try:
             np.save(cache, target)
         except OSError:
@@ -449,7 +451,7 @@ def run_ours(args):
     # step k iterates; step 0's upload sits inside its own bracket. Each step is bracketed on the
     # compute stream like the device-resident steps, L2 flushed between steps, outside the brackets.
     gm.timing(False)
-    tgt_host = torch.as_tensor(target[None]).pin_memory()
+    tgt_host = torch.as_tensor(np.ascontiguousarray(target[None])).pin_memory()
     loss_host = torch.empty(3).pin_memory()
     bufs = [torch.empty_like(tgt), torch.empty_like(tgt)]
     copy_stream = torch.cuda.Stream(device=dev)

@@ -116,6 +116,17 @@ template <int TILE, int PPT>
 struct Layout {
     static constexpr int kThreads = TILE * TILE / PPT;
     static constexpr int kBlocksX = TILE / 8;
+    // resident CTAs per SM the fused kernel is compiled for: 16 x 1 (8 warps a CTA) capped at 64
+    // registers for 4 CTAs instead of 3 (8-view 640x480 window: fused kernel 0.748 -> 0.645 ms;
+    // 5 CTAs 0.652, 6 CTAs 0.716); the other layouts are bounded by shared memory or are not
+    // helped
+    static constexpr int kMinBlocks = (TILE == 16 && PPT == 1) ? 4 : 1;
+    // the adjoint reuses the forward's staged batch and visit lists when the tile's whole list
+    // fits one batch, and then starts without CTA barriers (each warp cuts its own list at its
+    // own end): 16 x 1 window 0.645 -> 0.634 ms, 8 x 1 0.653 -> 0.636 ms; not for 16 x 2, where
+    // the warps' imbalance moves to the work queue's barrier (300k-Gaussian keyframe: 0.362 ->
+    // 0.383 ms)
+    static constexpr bool kReuseStaged = !(TILE == 16 && PPT == 2);
     __device__ static void pixel(int tid, int& lx, int& ly0) {
         const int w = tid >> 5, l = tid & 31;
         lx = (w % kBlocksX) * 8 + (l & 7);
@@ -261,8 +272,11 @@ __device__ __forceinline__ uint32_t warp_mask(const TileGeom<TILE, PPT>& g, cons
 // Forward compositing (Eq. 3) of a thread's PPT pixels over the tile's sorted
 // list. Returns final T, the colour, and per pixel the number of list entries
 // up to and including the last blended Gaussian; optionally the Eq. 8 argmax.
+// The return value is the length of the warp's visit list when the tile's whole
+// list was staged as one batch (it is left in shared memory for the adjoint),
+// else -1; which of the two is the same for every warp of the CTA.
 template <int TILE, int PPT, bool ARGMAX, bool DET>
-__device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const bool (&inside)[PPT],
+__device__ __forceinline__ int fwd_core(const TileGeom<TILE, PPT>& g, const bool (&inside)[PPT],
                                          const uint32_t* __restrict__ pval, const uint32_t* __restrict__ emit_item,
                                          const float4* __restrict__ rec, const DevConst& kc, float (&T)[PPT], float (&cr)[PPT], float (&cg)[PPT],
                                          float (&cb)[PPT], uint32_t (&last)[PPT], uint32_t (&amax)[PPT]) {
@@ -289,6 +303,7 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
         amax[p] = 0xFFFFFFFFu;
     }
     const uint2 rg = g.rg;
+    int staged = -1;
     for (uint32_t bs = rg.x; bs < rg.y; bs += kBatch) {
         if (__syncthreads_count(nlive > 0) == 0) break;
         for (int i = threadIdx.x; i < kBatch; i += NT) {
@@ -304,6 +319,7 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
         __syncthreads();
         const int cnt = min((uint32_t)kBatch, rg.y - bs);
         const int nk = build_warp_list(st, cnt, 0u, 0xFFFFFFFFu);
+        if (rg.y - rg.x <= (uint32_t)kBatch) staged = nk;
         const typename Stage<kBatch, NT / 32>::Idx* wl = st.list[threadIdx.x >> 5];
         int knext = nk > 0 ? (int)wl[0] : 0;   // the next entry's index is loaded one visit ahead
         // unrolled by two: the next entry's record loads and membership tests interleave with
@@ -357,6 +373,7 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
             }
         }
     }
+    return staged;
 }
 
 // Adjoint of the compositing for a thread's PPT pixels: walks the tile's list
@@ -367,13 +384,15 @@ __device__ __forceinline__ void fwd_core(const TileGeom<TILE, PPT>& g, const boo
 // kLaneAtomicMax lanes blended it, each adds its own 9 values with two float4
 // atomics and one scalar; else a warp sum, then one 9-lane atomic). Each
 // warp visits only the batch entries its compacted list holds, which stop at
-// the warp's largest last-blended entry.
+// the warp's largest last-blended entry. With staged >= 0 (the forward left the
+// tile's whole list staged, and this warp's visit list of that length) each
+// warp cuts its own list at its own end and walks it without a CTA barrier.
 template <int TILE, int PPT, bool DET>
 __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uint32_t* __restrict__ pval,
                                          const uint32_t* __restrict__ emit_item, const float4* __restrict__ rec,
                                          const DevConst& kc, float (&T)[PPT], const uint32_t (&cnt_last)[PPT],
                                          const float (&gr)[PPT], const float (&gg)[PPT], const float (&gb)[PPT],
-                                         float* __restrict__ grad2d, float* __restrict__ pairgrad) {
+                                         float* __restrict__ grad2d, float* __restrict__ pairgrad, int staged) {
     constexpr int NT = Layout<TILE, PPT>::kThreads;
     constexpr int kBatch = batch_for(NT);
     Stage<kBatch, NT / 32>& st = stage<kBatch, NT / 32>();
@@ -394,30 +413,45 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
         my_end[p] = rg.x + cnt_last[p];
         thread_end = max(thread_end, my_end[p]);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) smax = rg.x;
-    __syncthreads();
     const uint32_t wm = __reduce_max_sync(0xFFFFFFFFu, thread_end);
-    if (lane == 0) atomicMax(&smax, wm);
-    __syncthreads();
-    const uint32_t end = smax;
+    uint32_t end = wm;
+    if (staged < 0) {   // the CTA's largest end decides which batches are staged again
+        __syncthreads();
+        if (threadIdx.x == 0) smax = rg.x;
+        __syncthreads();
+        if (lane == 0) atomicMax(&smax, wm);
+        __syncthreads();
+        end = smax;
+    }
     const uint32_t warp_end = wm;
     for (uint32_t be = end; be > rg.x;) {
         const uint32_t bs = be - rg.x > (uint32_t)kBatch ? be - kBatch : rg.x;
-        __syncthreads();
-        for (int i = threadIdx.x; i < kBatch; i += NT) {
-            const uint32_t j = bs + i;
-            if (j < be) {
-                const uint32_t pv = pval[j];   // the item, or its emission index (deterministic mode)
-                const uint32_t item = DET ? emit_item[pv] : pv;
-                stage_record(rec, item, g.ox, g.oy, kc.alpha_min, s0[i], s1[i], s2[i]);
-                sid[i] = pv;
-                st.mask[i] = warp_mask<TILE, PPT>(g, s0[i], s1[i], s2[i].w);
-            }
-        }
-        __syncthreads();
-        const int nk = build_warp_list(st, (int)(be - bs), bs, warp_end);
         const typename Stage<kBatch, NT / 32>::Idx* wl = st.list[threadIdx.x >> 5];
+        int nk;
+        if (staged >= 0) {
+            // the forward's visit list (ascending) is still staged: cut it before the warp's end
+            int lo = 0, hi = staged;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (bs + (uint32_t)wl[mid] < warp_end) lo = mid + 1;
+                else hi = mid;
+            }
+            nk = lo;
+        } else {
+            __syncthreads();
+            for (int i = threadIdx.x; i < kBatch; i += NT) {
+                const uint32_t j = bs + i;
+                if (j < be) {
+                    const uint32_t pv = pval[j];   // the item, or its emission index (deterministic mode)
+                    const uint32_t item = DET ? emit_item[pv] : pv;
+                    stage_record(rec, item, g.ox, g.oy, kc.alpha_min, s0[i], s1[i], s2[i]);
+                    sid[i] = pv;
+                    st.mask[i] = warp_mask<TILE, PPT>(g, s0[i], s1[i], s2[i].w);
+                }
+            }
+            __syncthreads();
+            nk = build_warp_list(st, (int)(be - bs), bs, warp_end);
+        }
         int knext = nk > 0 ? (int)wl[nk - 1] : 0;   // as in the forward: one visit ahead
         for (int i = nk - 1; i >= 0; --i) {
             const int k = knext;
@@ -586,7 +620,7 @@ __global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
                 gb[p] = dLdC[(size_t)g.view * 3 * HW + 2 * HW + pix];
             }
         }
-        bwd_core<TILE, PPT, DET>(g, pval, emit_item, rec, kc, T, cnt, gr, gg, gb, grad2d, pairgrad);
+        bwd_core<TILE, PPT, DET>(g, pval, emit_item, rec, kc, T, cnt, gr, gg, gb, grad2d, pairgrad, -1);
     }
 }
 
@@ -595,7 +629,7 @@ __global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
 // pixels, then the adjoint, with final T, last index and dL/dC kept in
 // registers. Writes the image and one photometric partial sum per CTA.
 template <int TILE, int PPT, bool DET>
-__global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
+__global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads, Layout<TILE, PPT>::kMinBlocks)
     k_raster_fused(const uint2* __restrict__ ranges, const uint32_t* __restrict__ pval,
                    const float4* __restrict__ rec, int width, int height, int tiles_x, int tiles_per_view,
                    DevConst kc, const float* __restrict__ target, const float* const* __restrict__ target_slot,
@@ -613,7 +647,8 @@ __global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
         inside_mask(g, width, height, inside);
         float T[PPT], cr[PPT], cg[PPT], cb[PPT], gr[PPT], gg[PPT], gb[PPT];
         uint32_t last[PPT], amax[PPT];
-        fwd_core<TILE, PPT, false, DET>(g, inside, pval, emit_item, rec, kc, T, cr, cg, cb, last, amax);
+        const int staged =
+            fwd_core<TILE, PPT, false, DET>(g, inside, pval, emit_item, rec, kc, T, cr, cg, cb, last, amax);
         float tl = 0.f;   // this thread's photometric sum over the tile
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
@@ -648,7 +683,8 @@ __global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
             }
             __syncthreads();
         }
-        bwd_core<TILE, PPT, DET>(g, pval, emit_item, rec, kc, T, last, gr, gg, gb, grad2d, pairgrad);
+        bwd_core<TILE, PPT, DET>(g, pval, emit_item, rec, kc, T, last, gr, gg, gb, grad2d, pairgrad,
+                                 (DET || !Layout<TILE, PPT>::kReuseStaged) ? -1 : staged);
     }
     // per-CTA photometric partial (already scaled)
     __shared__ float red[32];

@@ -149,7 +149,8 @@ class Room:
         out = np.zeros((H * W, 3))
         for s in range(0, H * W, chunk):
             out[s:s + chunk] = self._shade(c, d_world[s:s + chunk])
-        return out.T.reshape(3, H, W).astype(np.float32)
+        # a C-contiguous array (the transpose alone is a strided view of the [H * W, 3] rows)
+        return np.ascontiguousarray(out.T.reshape(3, H, W), dtype=np.float32)
 
     def raycast_torch(self, cam: Camera, device="cuda", chunk: int = 65536):
         """The same ray-cast as ``raycast`` evaluated with float32 torch ops on ``device``
