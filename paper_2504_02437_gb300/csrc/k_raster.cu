@@ -116,11 +116,12 @@ template <int TILE, int PPT>
 struct Layout {
     static constexpr int kThreads = TILE * TILE / PPT;
     static constexpr int kBlocksX = TILE / 8;
-    // resident CTAs per SM the fused kernel is compiled for: 16 x 1 (8 warps a CTA) capped at 64
-    // registers for 4 CTAs instead of 3 (8-view 640x480 window: fused kernel 0.748 -> 0.645 ms;
-    // 5 CTAs 0.652, 6 CTAs 0.716); the other layouts are bounded by shared memory or are not
-    // helped
-    static constexpr int kMinBlocks = (TILE == 16 && PPT == 1) ? 4 : 1;
+    // resident CTAs per SM the fused kernel is compiled for (its register cap): 16 x 1 (8 warps a
+    // CTA) capped at 64 registers for 4 CTAs instead of 3 (8-view 640x480 window: fused kernel
+    // 0.748 -> 0.645 ms; 5 CTAs 0.652, 6 CTAs 0.716). 0 leaves the bound unset, so the others
+    // keep the compiler's own register count (an explicit bound of 1 let it take more: 16 x 2
+    // rose from 80 to 96 registers, 5 CTAs per SM instead of 6, 5 % slower)
+    static constexpr int kMinBlocks = (TILE == 16 && PPT == 1) ? 4 : 0;
     // the adjoint reuses the forward's staged batch and visit lists when the tile's whole list
     // fits one batch, and then starts without CTA barriers (each warp cuts its own list at its
     // own end): 16 x 1 window 0.645 -> 0.634 ms, 8 x 1 0.653 -> 0.636 ms; not for 16 x 2, where
