@@ -43,12 +43,15 @@ FLOP_FWD_TESTED, FLOP_FWD_BLENDED = 12, 10
 FLOP_BWD_WALKED, FLOP_BWD_BLENDED = 12, 50
 FP32_LANES_PER_SM = 128
 
-# DRAM bytes (read + write) of one launch of the dominant kernel from an ncu capture of this
+# DRAM bytes (read + write) of one launch of the dominant kernel from an ncu capture of each
 # workload, with the kernel source's sha256 and layout at capture time (the figure is reported
-# only while both still match): profiles/raster_fused_replica_1200x680_300k.md
+# only while both still match): profiles/raster_fused_replica_1200x680_300k.md (the keyframe)
+# and profiles/raster_fused_window_8x640x480_150k.md (the window)
+_RASTER_SHA = "fa5633b852399f2c59d159969a59812b46e8b8cb986563c689a395ede85e305d"
 NCU_TRAFFIC = {"raster_fused": {"bytes": 35.92e6, "source": "paper_2504_02437_gb300/csrc/k_raster.cu",
-                                "sha256": "fa6a8a25845b91562d05ca4950253eca2268dcff92e4030dbf47864e6a8dd82f",
-                                "tile": 16, "ppt": 2}}
+                                "sha256": _RASTER_SHA, "tile": 16, "ppt": 2},
+               "raster_fused_window": {"bytes": 102.10e6, "source": "paper_2504_02437_gb300/csrc/k_raster.cu",
+                                       "sha256": _RASTER_SHA, "tile": 16, "ppt": 1}}
 
 
 def _ncu_traffic(kernel: str, tile: int, ppt: int):
@@ -634,7 +637,9 @@ def window_measure(args, steps: int, device: int = 0) -> dict:
             "sequential": {"what": f"{V} single-view iterations (one per view, {V} Adam steps) per step",
                            "value": 1000.0 / ms_seq, "ms_per_step": ms_seq, "speedup_of_window": ms_seq / ms_window},
             "gpu_launches": int(launches), "work": work,
-            "roofline": dict(fused_roofline(work, fused_ms, n_sm, peaks), kernel="raster_fused"),
+            "roofline": dict(fused_roofline(work, fused_ms, n_sm, peaks), kernel="raster_fused",
+                             traffic=_ncu_traffic("raster_fused_window", tile, ppt),
+                             traffic_unit="bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"),
             "l2": "flushed between iterations (256 MB write)", "clocks": clk.summary()}
 
 
