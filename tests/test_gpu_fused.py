@@ -14,7 +14,10 @@ the parameters after the Adam step) for
   1,932 records per 16-px tile against 512-record batches; 1,492 per 8-px tile
   against 256), with low opacities so that pixels blend (and stop) deep inside
   the lists: the forward's batch loop and the adjoint's back-to-front walk
-  across batch boundaries.
+  across batch boundaries;
+* one-tile views whose list holds exactly one staging batch, and one batch
+  plus one record, at every layout: the adjoint reusing the forward's staged
+  batch, and staging again.
 """
 import numpy as np
 import pytest
@@ -222,3 +225,34 @@ def test_dense_bins_pairs_bit_exact(det):
     fwd = O.render(p.astype(np.float64), cam, flags=True)
     err = np.abs(rgb - fwd["rgb"]).max(axis=0)
     assert err[~fwd["near"]].max() <= IMG_ATOL
+
+
+def one_tile_scene(tile, k, seed=41):
+    """Exactly k Gaussians on a one-tile view (tile x tile pixels), every one certainly listed
+    in its only tile: candidates of log-scale N(-3.5, 0.3) and opacity logit N(-2, 1) whose
+    oracle screen mean lies at least 1.5 px inside the image, and which the oracle keeps
+    (depth past the near plane, positive determinant), the first k of them."""
+    c = tile / 2.0
+    p, cam = frustum_scene(n=4 * k, width=tile, height=tile, fx=2.0 * tile, fy=2.0 * tile, cx=c, cy=c,
+                           seed=seed, logscale_mean=-3.5, logscale_std=0.3, opacity_mean=-2.0)
+    pr = O.project(torch.as_tensor(p, dtype=torch.float64), cam)
+    inside = (pr["valid"] & ((pr["u"] - c).abs() < c - 1.5) & ((pr["v"] - c).abs() < c - 1.5)).numpy()
+    keep = np.nonzero(inside)[0][:k]
+    assert keep.size == k
+    return np.ascontiguousarray(p[:, keep]), cam, random_target(tile, tile, seed=seed + 1)
+
+
+@pytest.mark.parametrize("tile,ppt", LAYOUTS)
+@pytest.mark.parametrize("extra", [0, 1])
+def test_fused_iteration_at_the_staging_batch_boundary(tile, ppt, extra):
+    """A tile list of exactly one staging batch (the adjoint reuses the forward's staged batch
+    and, except at 16x2, starts without CTA barriers) and of one batch plus one record (the
+    adjoint stages the list again, in two batches)."""
+    threads = tile * tile // ppt
+    batch = 512 if threads >= 128 else 256
+    p, cam, tg = one_tile_scene(tile, batch + extra)
+    g, near, excl = oracle_ref(p, [cam], tg)
+    out = iterate_once(p, [cam], tg, tile_size=tile, pixels_per_thread=ppt)
+    assert _longest_list(out) == batch + extra
+    # a pixel of this small view near a discrete decision counts for 1 / tile^2 of the image
+    check_iteration(out, g, near, excl, p, max_near=0.05, floor_frac=GRAD_FLOOR_DEEP)
