@@ -255,4 +255,4 @@ def test_fused_iteration_at_the_staging_batch_boundary(tile, ppt, extra):
     out = iterate_once(p, [cam], tg, tile_size=tile, pixels_per_thread=ppt)
     assert _longest_list(out) == batch + extra
     # a pixel of this small view near a discrete decision counts for 1 / tile^2 of the image
-    check_iteration(out, g, near, excl, p, max_near=0.05, floor_frac=GRAD_FLOOR_DEEP)
+    check_iteration(out, g, near, excl, p, max_near=0.05)
