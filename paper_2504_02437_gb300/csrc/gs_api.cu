@@ -399,6 +399,7 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         ok = ok && dalloc(&c->offsets, V * cap) == cudaSuccess;
         ok = ok && dalloc(&c->ranges, (size_t)c->max_bins) == cudaSuccess;
         ok = ok && dalloc(&c->work_order, (size_t)c->max_bins) == cudaSuccess;
+        ok = ok && dalloc(&c->work_order_next, (size_t)c->max_bins) == cudaSuccess;
         ok = ok && dalloc(&c->T_final, V * maxpix) == cudaSuccess;
         ok = ok && dalloc(&c->n_last, V * maxpix) == cudaSuccess;
         ok = ok && dalloc(&c->dLdC, 3 * V * maxpix) == cudaSuccess;
@@ -423,7 +424,7 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         ok = ok && cudaMallocHost((void**)&c->hflags, sizeof(uint32_t) * 4) == cudaSuccess;
         ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
         ok = ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
-        for (int i = 0; i < 5; ++i)
+        for (int i = 0; i < 6; ++i)
             ok = ok && cudaEventCreateWithFlags(&c->side_ev[i], cudaEventDisableTiming) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&c->graph_done, cudaEventDisableTiming) == cudaSuccess;
         if (!ok) { code = fail(c, GS_ERR_OOM, "device allocation failed"); break; }
@@ -460,7 +461,7 @@ void gs_destroy(gs_ctx* c) {
     for (auto e : c->tpool) cudaEventDestroy(e);
     void* ptrs[] = {c->params, c->grads, c->adam_m, c->adam_v, c->dens_sum, c->dens_cnt, c->dom_cnt, c->adam_pw, c->dcam, c->rec,
                     c->tiles_touched, c->depth, c->dkey[0], c->dkey[1], c->dval[0], c->dval[1], c->offsets, c->ranges,
-                    c->work_order, c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->vis_blocks, (void*)c->target_slot, c->ssim_maps, c->ssim_part, c->dcount,
+                    c->work_order, c->work_order_next, c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->vis_blocks, (void*)c->target_slot, c->ssim_maps, c->ssim_part, c->dcount,
                     c->partials, c->psnr_part, c->reg_part, c->tile_part, c->fpart,
                     c->own_rgb};
     for (void* p : ptrs) cudaFree(p);
@@ -469,7 +470,7 @@ void gs_destroy(gs_ctx* c) {
     if (c->hflags) cudaFreeHost(c->hflags);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->side) cudaStreamDestroy(c->side);
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 6; ++i)
         if (c->side_ev[i]) cudaEventDestroy(c->side_ev[i]);
     if (c->graph_done) cudaEventDestroy(c->graph_done);
     delete c;
@@ -665,6 +666,9 @@ static int iteration_tail(gs_ctx* c, const DevConst& k, const float* target, con
         CK(launch_loss_tail(c, k, det ? c->tile_part : c->fpart, det ? c->n_bins : fgrid, loss_out, ts));
     }
     if (capture) CK(cudaMemcpyAsync(c->hflags, c->dcount, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, ts));
+    if (c->order_ahead)   // the compositing is done with the current order: the next one goes in place
+        CK(cudaMemcpyAsync(c->work_order, c->work_order_next, sizeof(uint32_t) * (size_t)c->n_bins,
+                           cudaMemcpyDeviceToDevice, ts));
     {
         Phase ph(c, GS_PHASE_PROJECT_BWD, s);
         CK(reduce_pair_grads(c, s));
@@ -866,6 +870,8 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
         ++c->launches;
         k_set_cams<<<1, 32, 0, cs>>>(b, c->dcam, c->target_slot);
         cc = side_begin(c, cs);
+        // the direct call above left this shape's work order in place for the first replay
+        c->order_ahead = true;
         if (cc == GS_OK) cc = front_half(c, k, cs);
         if (cc == GS_OK) cc = iteration_tail(c, k, target, c->target_slot, rgb, loss_out, true, cs);
     }
@@ -873,6 +879,7 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
     e = cudaStreamEndCapture(cs, &g);
     c->capturing = false;
     c->side_zeroed = false;
+    c->order_ahead = false;
     c->graph_kernels = c->launches - launches0;
     c->launches = launches0;
     if (cc != GS_OK || e != cudaSuccess || !g) {

@@ -148,9 +148,13 @@ struct gs_ctx {
     // overlapping the projection and the sorts, and the loss total runs there beside the
     // projection adjoint and Adam (a fork and joins, which a captured graph keeps as branches)
     cudaStream_t side = nullptr;
-    cudaEvent_t side_ev[5] = {};            // fork, overflow flag + ranges zeroed, grad2d zeroed,
-                                            // second fork, side work done
+    cudaEvent_t side_ev[6] = {};            // fork, overflow flag + ranges zeroed, grad2d zeroed,
+                                            // second fork, side work done, ranges ready
     bool side_zeroed = false;               // this iteration's zeroing was issued on `side`
+    // a replayed iteration composites in the longest-first order the previous one computed (any
+    // order of the same bins gives the same result) and computes the next order on `side`
+    bool order_ahead = false;
+    uint32_t* work_order_next = nullptr;    // [max bins]
     cudaEvent_t graph_done = nullptr;       // recorded after each replay
     bool graph_pending = false;             // a replay's flags have not been checked yet
     uint32_t* hflags = nullptr;             // pinned: [0] pairs, [1] overflow of the last replay

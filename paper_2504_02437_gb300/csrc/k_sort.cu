@@ -556,7 +556,15 @@ cudaError_t compute_ranges(gs_ctx* c, cudaStream_t s) {
     k_ranges<<<c->num_sms * 8, 256, 0, s>>>(c->pkey[c->pair_buf], c->dcount, (uint64_t)c->pair_cap,
                                             (uint32_t)c->n_bins, c->ranges);
     ++c->launches;
-    k_work_order<<<1, 1024, 0, s>>>(c->ranges, (uint32_t)c->n_bins, c->work_order);
+    if (c->order_ahead) {
+        // the next iteration's order, beside this one's compositing (which uses the order the
+        // previous iteration left); iteration_tail copies it into place after the compositing
+        cudaEventRecord(c->side_ev[5], s);
+        cudaStreamWaitEvent(c->side, c->side_ev[5], 0);
+        k_work_order<<<1, 1024, 0, c->side>>>(c->ranges, (uint32_t)c->n_bins, c->work_order_next);
+    } else {
+        k_work_order<<<1, 1024, 0, s>>>(c->ranges, (uint32_t)c->n_bins, c->work_order);
+    }
     return cudaGetLastError();
 }
 
