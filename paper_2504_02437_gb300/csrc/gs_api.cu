@@ -249,16 +249,17 @@ struct Phase {
     }
 };
 
-// The zeroing a mapping iteration needs before its pair emission (overflow flag, bin ranges)
-// and before its adjoint (screen gradients), issued on the side stream at the iteration's start
-// so that it runs beside the projection and the depth sort; back_half and iteration_tail wait
-// for it instead of zeroing on the main stream.
+// The zeroing a mapping iteration needs before its pair emission (overflow flag, compositing
+// work queues, bin ranges) and before its adjoint (screen gradients), issued on the side stream
+// at the iteration's start so that it runs beside the projection and the depth sort; back_half
+// and iteration_tail wait for it instead of zeroing on the main stream.
 int side_begin(gs_ctx* c, cudaStream_t s) {
     CK(cudaEventRecord(c->side_ev[0], s));
     CK(cudaStreamWaitEvent(c->side, c->side_ev[0], 0));
     CK(cudaMemsetAsync(c->dcount + 1, 0, sizeof(uint32_t), c->side));
+    CK(cudaMemsetAsync(c->dcount + 6, 0, 2 * sizeof(uint32_t), c->side));   // the compositing work queues
     CK(cudaMemsetAsync(c->ranges, 0, sizeof(uint2) * (size_t)c->n_bins, c->side));
-    CK(cudaEventRecord(c->side_ev[1], c->side));
+    CK(cudaEventRecord(c->side_ev[1], c->side));   // (waited for before the pair emission)
     CK(cudaMemsetAsync(c->grad2d, 0, sizeof(float) * kGrad2dStride * c->n_views * (size_t)c->n, c->side));
     CK(cudaEventRecord(c->side_ev[2], c->side));
     c->side_zeroed = true;
@@ -637,7 +638,7 @@ static int iteration_tail(gs_ctx* c, const DevConst& k, const float* target, con
             return fail(c, GS_ERR_CUDA, "loss launch", cudaGetLastError());
     }
     if (c->side_zeroed)
-        CK(cudaStreamWaitEvent(s, c->side_ev[2], 0));   // grad2d zeroed
+        CK(cudaStreamWaitEvent(s, c->side_ev[2], 0));   // work queues and grad2d zeroed
     else
         CK(cudaMemsetAsync(c->grad2d, 0, sizeof(float) * kGrad2dStride * c->n_views * (size_t)c->n, s));
     // the loss total (and, when capturing, the copy of the pair count and overflow flag) on the

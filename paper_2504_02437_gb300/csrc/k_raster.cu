@@ -839,7 +839,8 @@ static void fused_launch(gs_ctx* c, const DevConst& k, const float* target, cons
 cudaError_t launch_raster_forward(gs_ctx* c, const DevConst& k, float* rgb, int32_t* argmax, cudaStream_t s) {
     const int tpv = c->hcam[0].tiles_x * c->hcam[0].tiles_y;
     if (c->n_bins == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(c->dcount + 6, 0, sizeof(uint32_t), s);   // work queue
+    // work queue (a mapping iteration zeroes it on its side stream)
+    cudaError_t e = c->side_zeroed ? cudaSuccess : cudaMemsetAsync(c->dcount + 6, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     ++c->launches;
     GS_DISPATCH(fwd_launch, c, k, rgb, argmax, s, tpv);
@@ -849,7 +850,8 @@ cudaError_t launch_raster_forward(gs_ctx* c, const DevConst& k, float* rgb, int3
 cudaError_t launch_raster_backward(gs_ctx* c, const DevConst& k, const float* dLdC, cudaStream_t s) {
     const int tpv = c->hcam[0].tiles_x * c->hcam[0].tiles_y;
     if (c->n_bins == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(c->dcount + 7, 0, sizeof(uint32_t), s);   // work queue
+    // work queue (a mapping iteration zeroes it on its side stream)
+    cudaError_t e = c->side_zeroed ? cudaSuccess : cudaMemsetAsync(c->dcount + 7, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     ++c->launches;
     GS_DISPATCH(bwd_launch, c, k, dLdC, s, tpv);
@@ -861,7 +863,8 @@ cudaError_t launch_raster_fused(gs_ctx* c, const DevConst& k, const float* targe
     const int tpv = c->hcam[0].tiles_x * c->hcam[0].tiles_y;
     *grid_out = 0;
     if (c->n_bins == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(c->dcount + 6, 0, sizeof(uint32_t), s);   // work queue
+    // work queue (a mapping iteration zeroes it on its side stream)
+    cudaError_t e = c->side_zeroed ? cudaSuccess : cudaMemsetAsync(c->dcount + 6, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     ++c->launches;
     GS_DISPATCH(fused_launch, c, k, target, target_slot, rgb, s, tpv, partials, max_grid, grid_out);
