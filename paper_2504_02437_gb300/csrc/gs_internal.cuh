@@ -200,7 +200,6 @@ cudaError_t launch_preprocess_backward(gs_ctx* c, const DevConst& k, bool add_re
 cudaError_t radix_sort_pairs(gs_ctx* c, uint32_t** keys, uint32_t** vals, const uint32_t* n_dev, uint32_t n_max,
                              uint32_t n_hint, int bits, int* out_buf, cudaStream_t s);
 cudaError_t scan_tiles(gs_ctx* c, uint32_t n_max, const uint32_t* n_dev, cudaStream_t s);
-cudaError_t scan_blocks(uint32_t* a, uint32_t n, uint32_t* total_dev, cudaStream_t s);
 cudaError_t emit_pairs(gs_ctx* c, uint32_t n_items, const uint32_t* n_dev, cudaStream_t s);
 // exclusive scan of n u32 values (in may equal out); the total goes to *total_dev
 cudaError_t scan_u32(gs_ctx* c, const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* total_dev, cudaStream_t s);

@@ -247,31 +247,61 @@ __global__ void __launch_bounds__(256, 6) k_preprocess(const float* __restrict__
     }
 }
 
-// Order-keeping compaction of the visible items: CTA b (the items of preprocess
-// CTA b) writes its visible keys and values at the scanned offset block_off[b],
-// in item order, so equal depths keep ascending ids through the stable sort.
+// Order-keeping compaction of the visible items, in item order, so that equal depths keep
+// ascending ids through the stable sort. CTA B takes the items of projection CTAs 4B .. 4B + 3
+// (linear index view * gx + x): it first adds the visible counts of the projection CTAs before
+// them (a few thousand values at most, read straight from block_vis: no separate scan launch),
+// then writes each one's visible keys and items in turn; the last CTA writes the total.
+constexpr int kCompactSub = 4;
 __global__ void __launch_bounds__(256) k_compact_visible(const uint32_t* __restrict__ kin,
-                                                         const uint32_t* __restrict__ vin, int n,
-                                                         const uint32_t* __restrict__ block_off,
-                                                         uint32_t* __restrict__ kout, uint32_t* __restrict__ vout) {
+                                                         const uint32_t* __restrict__ vin, int n, int gx,
+                                                         int nblocks, const uint32_t* __restrict__ block_vis,
+                                                         uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                         uint32_t* __restrict__ total_out) {
     __shared__ uint32_t wsum[8];
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ uint32_t s_off;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const size_t item = (size_t)blockIdx.y * n + gid;
-    const uint32_t key = gid < n ? kin[item] : 0xFFFFFFFFu;
-    const bool vis = key != 0xFFFFFFFFu;
-    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, vis);
-    if (lane == 0) wsum[w] = __popc(bal);
-    __syncthreads();
-    uint32_t pre = 0;
-    for (int k = 0; k < w; ++k) pre += wsum[k];
-    if (vis) {
-        uint32_t lt;
-        asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-        const uint32_t pos = block_off[(size_t)blockIdx.y * gridDim.x + blockIdx.x] + pre + __popc(bal & lt);
-        kout[pos] = key;
-        vout[pos] = vin[item];
+    const int b0 = blockIdx.x * kCompactSub;
+    {
+        uint32_t pre = 0;
+        for (int b = threadIdx.x; b < b0; b += 256) pre += block_vis[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xFFFFFFFFu, pre, o);
+        if (lane == 0) wsum[w] = pre;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int k = 0; k < 8; ++k) t += wsum[k];
+            s_off = t;
+        }
+        __syncthreads();
     }
+    uint32_t off = s_off;
+    uint32_t lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    for (int j = 0; j < kCompactSub && b0 + j < nblocks; ++j) {
+        const int b = b0 + j, view = b / gx, gid = (b - view * gx) * 256 + threadIdx.x;
+        const size_t item = (size_t)view * n + gid;
+        const uint32_t key = gid < n ? kin[item] : 0xFFFFFFFFu;
+        const bool vis = key != 0xFFFFFFFFu;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, vis);
+        __syncthreads();   // the previous sub-block's counts have been read
+        if (lane == 0) wsum[w] = __popc(bal);
+        __syncthreads();
+        uint32_t pre = 0, cnt = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            pre += k < w ? wsum[k] : 0u;
+            cnt += wsum[k];
+        }
+        if (vis) {
+            const uint32_t pos = off + pre + __popc(bal & lt);
+            kout[pos] = key;
+            vout[pos] = vin[item];
+        }
+        off += cnt;
+    }
+    if (total_out != nullptr && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total_out = off;
 }
 
 // Six CTAs of 128 threads per SM (at most 85 registers): the kernel is latency-bound on its
@@ -443,13 +473,12 @@ cudaError_t launch_preprocess(gs_ctx* c, int n_views, const DevConst& k, cudaStr
     if (c->n == 0) return cudaSuccess;
     dim3 grid((c->n + 255) / 256, n_views);
     const uint32_t nblocks = grid.x * grid.y;
-    c->launches += 3;
+    c->launches += 2;
     k_preprocess<<<grid, 256, 0, s>>>(c->params, c->n, c->cap, c->dcam, k, c->tile, c->rec, c->tiles_touched,
                                        c->dkey[1], c->dval[1], c->depth, c->vis_blocks,
                                        k.lambda_reg / (float)c->n, c->reg_part);
-    cudaError_t e = scan_blocks(c->vis_blocks, nblocks, c->dcount + 8, s);
-    if (e != cudaSuccess) return e;
-    k_compact_visible<<<grid, 256, 0, s>>>(c->dkey[1], c->dval[1], c->n, c->vis_blocks, c->dkey[0], c->dval[0]);
+    k_compact_visible<<<(nblocks + kCompactSub - 1) / kCompactSub, 256, 0, s>>>(
+        c->dkey[1], c->dval[1], c->n, (int)grid.x, (int)nblocks, c->vis_blocks, c->dkey[0], c->dval[0], c->dcount + 8);
     return cudaGetLastError();
 }
 

@@ -72,45 +72,6 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
     }
 }
 
-// In-place exclusive scan of `len` counters with one block of 1024 threads,
-// walking the array in coalesced tiles of 1024 with a running carry.
-__global__ void __launch_bounds__(1024) k_scan_counts(uint32_t* __restrict__ a, uint32_t len,
-                                                      uint32_t* __restrict__ total_out) {
-    __shared__ uint32_t warp_sums[32];
-    __shared__ uint32_t carry;
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    if (t == 0) carry = 0;
-    __syncthreads();
-    for (uint32_t base = 0; base < len; base += 1024) {
-        const uint32_t i = base + t;
-        const uint32_t c = i < len ? a[i] : 0u;
-        uint32_t x = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) warp_sums[w] = x;
-        __syncthreads();
-        if (w == 0) {
-            uint32_t v = warp_sums[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xFFFFFFFFu, v, o);
-                if (lane >= o) v += y;
-            }
-            warp_sums[lane] = v;
-        }
-        __syncthreads();
-        const uint32_t before = carry;
-        if (i < len) a[i] = before + x - c + (w > 0 ? warp_sums[w - 1] : 0u);
-        __syncthreads();
-        if (t == 0) carry = before + warp_sums[31];
-        __syncthreads();
-    }
-    if (t == 0 && total_out != nullptr) *total_out = carry;
-}
-
 // Exclusive scan of each digit's row of block counts (one CTA per digit):
 // hist[d * G + b] <- sum of hist[d * G + b'] for b' < b; dtot[d] <- row total.
 __global__ void __launch_bounds__(256) k_digit_scan(uint32_t* __restrict__ hist, int G, uint32_t* __restrict__ dtot) {
@@ -276,18 +237,34 @@ __global__ void __launch_bounds__(256) k_tile_block_sums(const uint32_t* __restr
     }
 }
 
+// Exclusive scan of the slices of k_tile_block_sums: block b first adds the block sums of the
+// slices before its own (a few hundred values, read straight from bsum: no separate scan
+// launch), then scans its slice; the last block writes the total.
 __global__ void __launch_bounds__(256) k_tile_scan(const uint32_t* __restrict__ order,
                                                    const uint32_t* __restrict__ tiles, uint32_t n,
                                                    const uint32_t* __restrict__ n_dev,
-                                                   const uint32_t* __restrict__ bsum, uint32_t* __restrict__ off) {
+                                                   const uint32_t* __restrict__ bsum, uint32_t* __restrict__ off,
+                                                   uint32_t* __restrict__ total_out) {
     __shared__ uint32_t ws[8];
     __shared__ uint32_t carry;
     if (n_dev != nullptr) n = umin(n, *n_dev);
     uint32_t begin, end;
     slice_of(n, gridDim.x, blockIdx.x, begin, end);
-    if (threadIdx.x == 0) carry = bsum[blockIdx.x];
-    __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    {
+        uint32_t pre = 0;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += 256) pre += bsum[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xFFFFFFFFu, pre, o);
+        if (lane == 0) ws[w] = pre;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int k = 0; k < 8; ++k) t += ws[k];
+            carry = t;
+        }
+        __syncthreads();
+    }
     for (uint32_t base = begin; base < end; base += 256) {
         uint32_t i = base + threadIdx.x;
         uint32_t c = i < end ? tiles[order ? order[i] : i] : 0u;
@@ -311,6 +288,7 @@ __global__ void __launch_bounds__(256) k_tile_scan(const uint32_t* __restrict__ 
         if (threadIdx.x == 0) carry += tot;
         __syncthreads();
     }
+    if (total_out != nullptr && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total_out = carry;
 }
 
 // Pair emission: item k of the depth order owns pairs off[k] .. off[k] + tiles
@@ -484,25 +462,18 @@ cudaError_t radix_sort_pairs(gs_ctx* c, uint32_t** keys, uint32_t** vals, const 
 cudaError_t scan_tiles(gs_ctx* c, uint32_t n_max, const uint32_t* n_dev, cudaStream_t s) {
     // the depth-sorted order is in dval[0] after the even number (4) of depth passes
     const int G = c->sort_blocks;
-    c->launches += 3;
+    c->launches += 2;
     k_tile_block_sums<<<G, 256, 0, s>>>(c->dval[0], c->tiles_touched, n_max, n_dev, c->hist);
-    k_scan_counts<<<1, 1024, 0, s>>>(c->hist, (uint32_t)G, c->dcount);
-    k_tile_scan<<<G, 256, 0, s>>>(c->dval[0], c->tiles_touched, n_max, n_dev, c->hist, c->offsets);
-    return cudaGetLastError();
-}
-
-cudaError_t scan_blocks(uint32_t* a, uint32_t n, uint32_t* total_dev, cudaStream_t s) {
-    k_scan_counts<<<1, 1024, 0, s>>>(a, n, total_dev);
+    k_tile_scan<<<G, 256, 0, s>>>(c->dval[0], c->tiles_touched, n_max, n_dev, c->hist, c->offsets, c->dcount);
     return cudaGetLastError();
 }
 
 cudaError_t scan_u32(gs_ctx* c, const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* total_dev,
                      cudaStream_t s) {
     const int G = c->sort_blocks;
-    c->launches += 3;
+    c->launches += 2;
     k_tile_block_sums<<<G, 256, 0, s>>>(nullptr, in, n, nullptr, c->hist);
-    k_scan_counts<<<1, 1024, 0, s>>>(c->hist, (uint32_t)G, total_dev);
-    k_tile_scan<<<G, 256, 0, s>>>(nullptr, in, n, nullptr, c->hist, out);
+    k_tile_scan<<<G, 256, 0, s>>>(nullptr, in, n, nullptr, c->hist, out, total_dev);
     return cudaGetLastError();
 }
 
