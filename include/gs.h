@@ -136,6 +136,12 @@ GS_API int gs_get_params(gs_ctx* ctx, float* params_dev, void* stream);
 /* Copy the gradient of the last gs_backward ([14][n] float32, row stride n). */
 GS_API int gs_get_grads(gs_ctx* ctx, float* grads_dev, void* stream);
 
+/* Overwrite the gradient that the next gs_step applies with grads_dev
+ * ([14][n] float32, row stride n = gs_num_gaussians; caller-owned, read
+ * before the call's work on `stream` completes), for a loss computed outside
+ * the library. Errors: GS_ERR_ARG (NULL with n > 0). */
+GS_API int gs_set_grads(gs_ctx* ctx, const float* grads_dev, void* stream);
+
 /* Map initialisation from back-projected patch centres (Eq. 6, Section 3.2
  * "Map Initialization"): appends one Gaussian per point of points_dev
  * ([n][3] world xyz) with colour rgb_dev ([n][3]) and the plain
@@ -152,7 +158,9 @@ GS_API int gs_init_map(gs_ctx* ctx, const float* points_dev, const float* rgb_de
  * largest blend weight (Eq. 8), -1 where nothing blends.
  * Keeps the per-pixel state that gs_backward needs. Synchronises the stream
  * once to size the pair buffers. Errors: GS_ERR_ARG, GS_ERR_CAPACITY (pair
- * buffer too small; the context grows it when possible), GS_ERR_CUDA. */
+ * buffer too small; the context grows it when possible), GS_ERR_CUDA,
+ * GS_ERR_NONFINITE (an earlier loss or gradient was not finite; reported once,
+ * the render is not made). */
 GS_API int gs_render(gs_ctx* ctx, const gs_camera* cams_host, int n_views, float* rgb_dev, float* T_dev,
               int32_t* argmax_dev, void* stream);
 
@@ -171,7 +179,9 @@ GS_API int gs_loss(gs_ctx* ctx, const float* target_dev, float* loss_dev, void* 
  * (no per-Gaussian blend state is stored). Errors: GS_ERR_STATE if no render. */
 GS_API int gs_backward(gs_ctx* ctx, const float* dL_drgb_dev, void* stream);
 
-/* One Adam step on every parameter with the gradient of the last gs_backward. */
+/* One Adam step on every parameter with the gradient of the last gs_backward.
+ * A parameter whose gradient is not finite keeps its value and moments; the
+ * next gs_render or gs_iterate then returns GS_ERR_NONFINITE (once). */
 GS_API int gs_step(gs_ctx* ctx, void* stream);
 
 /* One full mapping iteration (Section 3.2 "Map Optimization") over a window
@@ -188,7 +198,10 @@ GS_API int gs_step(gs_ctx* ctx, void* stream);
  * the deterministic mode, which has one layout and adds a fixed-order
  * per-Gaussian sum of the adjoint's per-pair gradients). An
  * overflow of the pair buffer during a replay skips that iteration's Adam
- * step; a later call then grows the buffer and returns GS_ERR_CAPACITY. */
+ * step; a later call then grows the buffer and returns GS_ERR_CAPACITY. A
+ * non-finite loss, or a non-finite gradient (its parameter and moments are
+ * left unchanged by the Adam step), makes a later call return
+ * GS_ERR_NONFINITE once, before it does any work. */
 GS_API int gs_iterate(gs_ctx* ctx, const gs_camera* cams_host, int n_views, const float* target_dev,
                float* loss_dev, float* rgb_dev, void* stream);
 

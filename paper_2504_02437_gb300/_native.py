@@ -55,6 +55,7 @@ SIGNATURES = {
     "gs_set_params": (_I, [_P, _P, _I, _P]),
     "gs_get_params": (_I, [_P, _P, _P]),
     "gs_get_grads": (_I, [_P, _P, _P]),
+    "gs_set_grads": (_I, [_P, _P, _P]),
     "gs_init_map": (_I, [_P, _P, _P, _I, _P]),
     "gs_render": (_I, [_P, C.POINTER(gs_camera), _I, _P, _P, _P, _P]),
     "gs_loss": (_I, [_P, _P, _P, _P]),

@@ -136,6 +136,14 @@ class GaussianMap:
         self._check(self.lib.gs_get_grads(self.ctx, _ptr(out), _stream()))
         return out
 
+    def set_grads(self, grads: torch.Tensor):
+        """The gradient the next step() applies ([14, n]), e.g. of a loss computed outside."""
+        g = grads.detach().to(device=f"cuda:{self.device}", dtype=torch.float32).contiguous()
+        if tuple(g.shape) != (14, self.n):
+            raise ValueError("grads must be [14, n]")
+        self._check(self.lib.gs_set_grads(self.ctx, _ptr(g), _stream()))
+        self._keep = g   # alive until the copy on the stream has run
+
     def init_map(self, points: torch.Tensor, rgb: torch.Tensor):
         pts = points.to(torch.float32).contiguous()
         col = rgb.to(torch.float32).contiguous()

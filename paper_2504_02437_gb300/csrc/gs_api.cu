@@ -249,6 +249,18 @@ struct Phase {
     }
 };
 
+// A non-finite loss or gradient of an earlier iteration (dcount[10], set by the loss total and
+// by Adam, which leaves a parameter with a non-finite gradient unchanged) is reported once by
+// the next call that reads the device flags, then cleared.
+int check_nonfinite(gs_ctx* c, uint32_t flag, cudaStream_t s) {
+    if (flag == 0u) return GS_OK;
+    CK(cudaMemsetAsync(c->dcount + 10, 0, sizeof(uint32_t), s));
+    c->hflags[10] = 0u;
+    return fail(c, GS_ERR_NONFINITE,
+                "an earlier iteration had a non-finite loss or gradient (parameters whose gradient was not "
+                "finite were left unchanged)");
+}
+
 // The zeroing a mapping iteration needs before its pair emission (overflow flag, compositing
 // work queues, bin ranges) and before its adjoint (screen gradients), issued on the side stream
 // at the iteration's start so that it runs beside the projection and the depth sort; back_half
@@ -422,7 +434,7 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         ok = ok && dalloc(&c->fpart, (size_t)c->n_fpart) == cudaSuccess;
         ok = ok && alloc_pairs(c, pc) == cudaSuccess;
         ok = ok && cudaMallocHost((void**)&c->hcount, sizeof(uint32_t) * 16) == cudaSuccess;
-        ok = ok && cudaMallocHost((void**)&c->hflags, sizeof(uint32_t) * 4) == cudaSuccess;
+        ok = ok && cudaMallocHost((void**)&c->hflags, sizeof(uint32_t) * 16) == cudaSuccess;
         ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
         ok = ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
         for (int i = 0; i < 6; ++i)
@@ -532,6 +544,15 @@ int gs_get_grads(gs_ctx* c, float* out, void* stream) {
     return GS_OK;
 }
 
+int gs_set_grads(gs_ctx* c, const float* in, void* stream) {
+    if (!c) return GS_ERR_ARG;
+    if (c->n == 0) return GS_OK;
+    if (!in) return fail(c, GS_ERR_ARG, "grads_dev is NULL");
+    CK(cudaMemcpy2DAsync(c->grads, sizeof(float) * c->cap, in, sizeof(float) * c->n, sizeof(float) * c->n,
+                         kParamRows, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return GS_OK;
+}
+
 int gs_render(gs_ctx* c, const gs_camera* cams, int n_views, float* rgb, float* T, int32_t* argmax, void* stream) {
     if (!c) return GS_ERR_ARG;
     if (!rgb) return fail(c, GS_ERR_ARG, "rgb_dev is NULL");
@@ -548,8 +569,12 @@ int gs_render(gs_ctx* c, const gs_camera* cams, int n_views, float* rgb, float* 
     if (c->n == 0) return render_empty(c, rgb, T, argmax, s);
     if ((code = front_half(c, k, s)) != GS_OK) return code;
     // size the pair buffers: read P back (the one synchronisation of a render)
-    CK(cudaMemcpyAsync(c->hcount, c->dcount, sizeof(uint32_t) * 9, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->hcount, c->dcount, sizeof(uint32_t) * 11, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if ((code = check_nonfinite(c, c->hcount[10], s)) != GS_OK) {
+        c->n_views = 0;
+        return code;
+    }
     const int64_t P = c->hcount[0];
     c->visible_hint = c->hcount[8];
     c->pairs_hint = (uint32_t)std::min<int64_t>(P, 0xFFFFFFFFll);
@@ -666,7 +691,7 @@ static int iteration_tail(gs_ctx* c, const DevConst& k, const float* target, con
         const bool det = c->tile_part != nullptr;
         CK(launch_loss_tail(c, k, det ? c->tile_part : c->fpart, det ? c->n_bins : fgrid, loss_out, ts));
     }
-    if (capture) CK(cudaMemcpyAsync(c->hflags, c->dcount, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, ts));
+    if (capture) CK(cudaMemcpyAsync(c->hflags, c->dcount, sizeof(uint32_t) * 11, cudaMemcpyDeviceToHost, ts));
     if (c->order_ahead)   // the compositing is done with the current order: the next one goes in place
         CK(cudaMemcpyAsync(c->work_order, c->work_order_next, sizeof(uint32_t) * (size_t)c->n_bins,
                            cudaMemcpyDeviceToDevice, ts));
@@ -774,6 +799,7 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
     if (c->graph && c->graph_pending && cudaEventQuery(c->graph_done) == cudaSuccess) {
         c->graph_pending = false;
         const uint32_t P = c->hflags[0];
+        if (c->hflags[10] != 0u) return check_nonfinite(c, c->hflags[10], s);
         if (c->hflags[1] != 0u) {
             drop_graph(c);
             if (alloc_pairs(c, std::min<int64_t>((int64_t)P + P / 2 + 4096, kMaxPairs)) != cudaSuccess)
@@ -840,8 +866,9 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
     CK(cudaGetLastError());
     if ((code = side_begin(c, s)) != GS_OK) return code;
     if ((code = front_half(c, k, s)) != GS_OK) return code;
-    CK(cudaMemcpyAsync(c->hcount, c->dcount, sizeof(uint32_t) * 9, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->hcount, c->dcount, sizeof(uint32_t) * 11, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if ((code = check_nonfinite(c, c->hcount[10], s)) != GS_OK) return code;
     {
         const int64_t P = c->hcount[0];
         c->visible_hint = c->hcount[8];

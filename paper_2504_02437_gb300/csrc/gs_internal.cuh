@@ -122,7 +122,9 @@ struct gs_ctx {
     int sort_blocks = 0;
     uint32_t* dcount = nullptr;             // device scalars [16]: [0] pairs, [1] overflow, [2] Adam
                                             // ticket, [3] UINT32_MAX, [4] Adam steps, [5] totals,
-                                            // [6], [7] work queues, [8] visible (view, Gaussian) items
+                                            // [6], [7] work queues, [8] visible (view, Gaussian) items,
+                                            // [10] a non-finite loss or gradient was seen (sticky until
+                                            // a call reports it)
     uint32_t* vis_blocks = nullptr;         // visible items per preprocess CTA, then their offsets
     uint32_t visible_hint = 0;              // host copy of dcount[8] from the last synchronising render
     uint32_t* hcount = nullptr;             // pinned host mirror

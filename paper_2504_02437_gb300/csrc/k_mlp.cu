@@ -636,7 +636,7 @@ int gs_mlp_forward(gs_mlp* M, const float* feat_dev, int n, float* out_dev, void
     if (!M || n < 0 || (n > 0 && (!feat_dev || !out_dev))) return GS_ERR_ARG;
     if (n == 0) return GS_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    if (*M->herr != 0u) return GS_ERR_CUDA;   // a tensor-core wait of an earlier call gave up
+    if (*M->herr != 0u) return GS_ERR_TIMEOUT;   // a tensor-core wait of an earlier call gave up
     if (mlp_rows(M, n) != GS_OK) return GS_ERR_OOM;
     if (mlp_forward_rows(M, feat_dev, n, s) != cudaSuccess) return GS_ERR_CUDA;
     if (cudaMemcpyAsync(out_dev, M->y, sizeof(float) * (size_t)n * kOutPad, cudaMemcpyDeviceToDevice, s) !=
@@ -650,7 +650,7 @@ int gs_mlp_forward(gs_mlp* M, const float* feat_dev, int n, float* out_dev, void
 int gs_mlp_backward(gs_mlp* M, const float* feat_dev, const float* target_dev, int n, float* loss_dev, void* stream) {
     if (!M || n <= 0 || !feat_dev || !target_dev) return GS_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    if (*M->herr != 0u) return GS_ERR_CUDA;   // a tensor-core wait of an earlier call gave up
+    if (*M->herr != 0u) return GS_ERR_TIMEOUT;   // a tensor-core wait of an earlier call gave up
     if (mlp_rows(M, n) != GS_OK) return GS_ERR_OOM;
     if (mlp_forward_rows(M, feat_dev, n, s) != cudaSuccess) return GS_ERR_CUDA;
     const bf16* W2 = M->wb + kHid * kIn;

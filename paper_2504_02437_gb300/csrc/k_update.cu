@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kRedThreads) k_l1(const float* __restrict__ rg
 // and CTA trees are fixed, so the result does not vary from run to run.
 __global__ void __launch_bounds__(kRedThreads) k_loss_final(const float* __restrict__ photo, int n_photo,
                                                             const float* __restrict__ reg, int n_reg,
-                                                            float* __restrict__ out) {
+                                                            float* __restrict__ out, uint32_t* __restrict__ nonfinite) {
     __shared__ double sa[kRedThreads / 32], sb[kRedThreads / 32];
     double a = 0.0, b = 0.0;
     for (int i = threadIdx.x; i < n_photo; i += kRedThreads) a += photo[i];
@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(kRedThreads) k_loss_final(const float* __restr
         out[0] = (float)(ta + tb);
         out[1] = (float)ta;
         out[2] = (float)tb;
+        if (!isfinite(ta + tb)) atomicOr(nonfinite, 1u);   // reported by a later call of the library
     }
 }
 
@@ -94,7 +95,15 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, const float
     __syncthreads();
     if (sbc[2] == 0.f) {
         const float ibc1 = sbc[0], ibc2 = sbc[1];   // 1 / (1 - beta^t)
-        auto upd = [&](float& p, float g, float& m, float& v, float lr) { adam_update(p, g, m, v, lr, a, ibc1, ibc2); };
+        // a non-finite gradient leaves its parameter and moments as they are (and is reported)
+        bool bad = false;
+        auto upd = [&](float& p, float g, float& m, float& v, float lr) {
+            if (!isfinite(g)) {
+                bad = true;
+                return;
+            }
+            adam_update(p, g, m, v, lr, a, ibc1, ibc2);
+        };
         // grid-stride over the 14 rows x ceil(n / 4) groups of 4 parameters
         const uint32_t nvec = (uint32_t)(n + 3) / 4u, total = nvec * (uint32_t)kParamRows;
         for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
@@ -118,6 +127,7 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ P, const float
                     upd(P[k + e], G[k + e], M[k + e], V[k + e], lr);
             }
         }
+        if (bad) atomicOr(st + 10, 1u);
     }
     if (threadIdx.x == 0) adam_bias_end(st, pw, sbc, spw, gridDim.x);
 }
@@ -186,7 +196,7 @@ cudaError_t launch_loss(gs_ctx* c, const DevConst& k, const float* rgb, const fl
     const float scale = k.lambda_color / (float)(3 * HW);
     c->launches += 2;
     k_l1<<<nb_img, kRedThreads, 0, s>>>(rgb, target, total, scale, c->dLdC, c->partials);
-    k_loss_final<<<1, kRedThreads, 0, s>>>(c->partials, nb_img, c->reg_part, reg_partials(c), loss_out);
+    k_loss_final<<<1, kRedThreads, 0, s>>>(c->partials, nb_img, c->reg_part, reg_partials(c), loss_out, c->dcount + 10);
     return cudaGetLastError();
 }
 
@@ -194,7 +204,8 @@ cudaError_t launch_loss_tail(gs_ctx* c, const DevConst& k, const float* photo_pa
                              float* loss_out, cudaStream_t s) {
     (void)k;
     ++c->launches;
-    k_loss_final<<<1, kRedThreads, 0, s>>>(photo_partials, n_photo, c->reg_part, reg_partials(c), loss_out);
+    k_loss_final<<<1, kRedThreads, 0, s>>>(photo_partials, n_photo, c->reg_part, reg_partials(c), loss_out,
+                                           c->dcount + 10);
     return cudaGetLastError();
 }
 
