@@ -413,6 +413,7 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         ok = ok && dalloc(&c->ranges, (size_t)c->max_bins) == cudaSuccess;
         ok = ok && dalloc(&c->work_order, (size_t)c->max_bins) == cudaSuccess;
         ok = ok && dalloc(&c->work_order_next, (size_t)c->max_bins) == cudaSuccess;
+        ok = ok && dalloc(&c->work_order_graph, (size_t)c->max_bins) == cudaSuccess;
         ok = ok && dalloc(&c->T_final, V * maxpix) == cudaSuccess;
         ok = ok && dalloc(&c->n_last, V * maxpix) == cudaSuccess;
         ok = ok && dalloc(&c->dLdC, 3 * V * maxpix) == cudaSuccess;
@@ -474,7 +475,7 @@ void gs_destroy(gs_ctx* c) {
     for (auto e : c->tpool) cudaEventDestroy(e);
     void* ptrs[] = {c->params, c->grads, c->adam_m, c->adam_v, c->dens_sum, c->dens_cnt, c->dom_cnt, c->adam_pw, c->dcam, c->rec,
                     c->tiles_touched, c->depth, c->dkey[0], c->dkey[1], c->dval[0], c->dval[1], c->offsets, c->ranges,
-                    c->work_order, c->work_order_next, c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->vis_blocks, (void*)c->target_slot, c->ssim_maps, c->ssim_part, c->dcount,
+                    c->work_order, c->work_order_next, c->work_order_graph, c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->vis_blocks, (void*)c->target_slot, c->ssim_maps, c->ssim_part, c->dcount,
                     c->partials, c->psnr_part, c->reg_part, c->tile_part, c->fpart,
                     c->own_rgb};
     for (void* p : ptrs) cudaFree(p);
@@ -885,6 +886,9 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
     c->adam_t += 1;
     c->rendered_rgb = rgb;
     const int64_t launches0 = c->launches;
+    // the first replay composites in the order this direct call computed for the shape
+    CK(cudaMemcpyAsync(c->work_order_graph, c->work_order, sizeof(uint32_t) * (size_t)c->n_bins,
+                       cudaMemcpyDeviceToDevice, s));
     c->cap_phases.clear();
     c->capturing = true;
     cudaStream_t cs = c->cap_stream;
@@ -898,8 +902,10 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
         ++c->launches;
         k_set_cams<<<1, 32, 0, cs>>>(b, c->dcam, c->target_slot);
         cc = side_begin(c, cs);
-        // the direct call above left this shape's work order in place for the first replay
+        // the direct call above left this shape's work order in work_order_graph for the first
+        // replay; every replay reads that buffer and writes the next order into it
         c->order_ahead = true;
+        std::swap(c->work_order, c->work_order_graph);
         if (cc == GS_OK) cc = front_half(c, k, cs);
         if (cc == GS_OK) cc = iteration_tail(c, k, target, c->target_slot, rgb, loss_out, true, cs);
     }
@@ -907,6 +913,7 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
     e = cudaStreamEndCapture(cs, &g);
     c->capturing = false;
     c->side_zeroed = false;
+    if (c->order_ahead) std::swap(c->work_order, c->work_order_graph);
     c->order_ahead = false;
     c->graph_kernels = c->launches - launches0;
     c->launches = launches0;

@@ -104,7 +104,8 @@ struct gs_ctx {
     uint32_t* emit_item = nullptr;          // [pair capacity]
     float* pairgrad = nullptr;              // [pair capacity * 9]
     float* tile_part = nullptr;             // [max bins] photometric loss per (view, tile)
-    uint32_t* work_order = nullptr;         // [max bins] bins by decreasing pair count
+    uint32_t* work_order = nullptr;         // [max bins] bins by decreasing pair count (while a
+                                            // replay is captured: the graph's own buffer)
     int max_bins = 0;
     float* T_final = nullptr;               // [max_views * H * W]
     uint32_t* n_last = nullptr;             // [max_views * H * W] entries up to the last blended
@@ -157,6 +158,9 @@ struct gs_ctx {
     // order of the same bins gives the same result) and computes the next order on `side`
     bool order_ahead = false;
     uint32_t* work_order_next = nullptr;    // [max bins]
+    uint32_t* work_order_graph = nullptr;   // [max bins] the order a replay composites in: its own
+                                            // buffer, so that a render of another shape between
+                                            // replays (which writes work_order) cannot change it
     cudaEvent_t graph_done = nullptr;       // recorded after each replay
     bool graph_pending = false;             // a replay's flags have not been checked yet
     uint32_t* hflags = nullptr;             // pinned: [0] pairs, [1] overflow of the last replay

@@ -256,3 +256,26 @@ def test_fused_iteration_at_the_staging_batch_boundary(tile, ppt, extra):
     assert _longest_list(out) == batch + extra
     # a pixel of this small view near a discrete decision counts for 1 / tile^2 of the image
     check_iteration(out, g, near, excl, p, max_near=0.05)
+
+
+def test_render_of_another_shape_between_replays(small):
+    """A replayed iteration composites in the order the previous replay left in the graph's own
+    buffer; a gs_render of another shape in between (which writes the context's work order)
+    must not change it. Deterministic mode: the two maps end bit for bit equal."""
+    p, cam, _, _, _, _ = small
+    cams = [cam, rotated_cam(cam, [0.03, -0.05, 0.01], [0.05, 0.0, 0.1]),
+            rotated_cam(cam, [-0.02, 0.06, 0.0], [-0.08, 0.02, -0.05])]
+    tg = cuda(random_target(160, 120, seed=5, n_views=3))
+    out = []
+    for interleave in (False, True):
+        gm = new_map(p.shape[1], views=3, deterministic=1)
+        gm.set_params(cuda(p))
+        loss = torch.empty(3, device="cuda")
+        for it in range(4):
+            gm.iterate(cams, tg, loss)
+            if interleave and it == 1:
+                gm.render(cams[0])   # one view: a third of the bins
+        torch.cuda.synchronize()
+        out.append(gm.params().cpu().numpy())
+        gm.close()
+    assert np.array_equal(out[0], out[1])
