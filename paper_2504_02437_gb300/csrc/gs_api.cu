@@ -650,7 +650,8 @@ int gs_step(gs_ctx* c, void* stream) {
 // compositing + loss + adjoint (one fused kernel with pure L1; forward, SSIM loss and
 // adjoint as three kernels with the SSIM term), the loss total, the projection adjoint
 // and Adam. Shared by the direct first call of gs_iterate and its graph capture; a
-// captured iteration also copies the pair count and overflow flag to the host.
+// captured iteration also copies the device flags (pair count, overflow, non-finite values) to
+// the host, where the next call reads them.
 static int iteration_tail(gs_ctx* c, const DevConst& k, const float* target, const float* const* slot, float* rgb,
                           float* loss_out, bool capture, cudaStream_t s) {
     const bool ssim = c->cfg.lambda_photo > 0.f;
@@ -667,8 +668,8 @@ static int iteration_tail(gs_ctx* c, const DevConst& k, const float* target, con
         CK(cudaStreamWaitEvent(s, c->side_ev[2], 0));   // work queues and grad2d zeroed
     else
         CK(cudaMemsetAsync(c->grad2d, 0, sizeof(float) * kGrad2dStride * c->n_views * (size_t)c->n, s));
-    // the loss total (and, when capturing, the copy of the pair count and overflow flag) on the
-    // side stream, beside the projection adjoint and Adam
+    // the loss total (and, when capturing, the copy of the device flags: pair count, overflow,
+    // non-finite values) on the side stream, beside the projection adjoint and Adam
     cudaStream_t ts = c->side_zeroed ? c->side : s;
     if (ssim) {
         Phase ph(c, GS_PHASE_RASTER_BWD, s);

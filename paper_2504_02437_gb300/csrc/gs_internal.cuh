@@ -163,7 +163,7 @@ struct gs_ctx {
                                             // replays (which writes work_order) cannot change it
     cudaEvent_t graph_done = nullptr;       // recorded after each replay
     bool graph_pending = false;             // a replay's flags have not been checked yet
-    uint32_t* hflags = nullptr;             // pinned: [0] pairs, [1] overflow of the last replay
+    uint32_t* hflags = nullptr;             // pinned [16]: dcount[0..10] as the last replay left them
     cudaGraphNode_t cam_node = nullptr;     // kernel node that uploads the cameras
     int64_t graph_kernels = 0;              // kernels per replay
     bool capturing = false;
