@@ -57,3 +57,25 @@ def test_sample_tiles_cover_the_image():
     assert all(0 <= x <= bench.W - 16 and 0 <= y <= bench.H - 16 for x, y in t)
     quad = [(x >= (bench.W - 16) / 2, y >= (bench.H - 16) / 2) for x, y in t[:32]]
     assert all(quad.count(q) == 8 for q in set(quad)) and len(set(quad)) == 4
+
+
+def test_traffic_is_reported_only_for_the_captured_source_and_layout():
+    """The DRAM traffic on the bench line comes from an ncu capture of one kernel source and
+    layout; it is reported while the source's sha256 and the layout still match, else null."""
+    sys.path.insert(0, ROOT)
+    import hashlib
+    import bench
+    for kernel, entry in bench.NCU_TRAFFIC.items():
+        src = os.path.join(ROOT, entry["source"])
+        matches = hashlib.sha256(open(src, "rb").read()).hexdigest() == entry["sha256"]
+        got = bench._ncu_traffic(kernel, entry["tile"], entry["ppt"])
+        assert got == (entry["bytes"] if matches else None)
+        # another layout never borrows the figure
+        assert bench._ncu_traffic(kernel, entry["tile"], entry["ppt"] + 8) is None
+    assert bench._ncu_traffic("no_such_kernel", 16, 2) is None
+    saved = dict(bench.NCU_TRAFFIC["raster_fused"])
+    try:
+        bench.NCU_TRAFFIC["raster_fused"]["sha256"] = "0" * 64
+        assert bench._ncu_traffic("raster_fused", saved["tile"], saved["ppt"]) is None
+    finally:
+        bench.NCU_TRAFFIC["raster_fused"].update(saved)
