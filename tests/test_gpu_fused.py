@@ -279,3 +279,31 @@ def test_render_of_another_shape_between_replays(small):
         out.append(gm.params().cpu().numpy())
         gm.close()
     assert np.array_equal(out[0], out[1])
+
+
+def test_phase_timing_does_not_change_results(small):
+    """Per-phase timing adds event-record nodes to the captured iteration (on both of its
+    branches); the arithmetic is the same with and without them. Deterministic mode, 3-view
+    window: bit for bit, and every phase was timed."""
+    p, cam, _, _, _, _ = small
+    cams = [cam, rotated_cam(cam, [0.03, -0.05, 0.01], [0.05, 0.0, 0.1]),
+            rotated_cam(cam, [-0.02, 0.06, 0.0], [-0.08, 0.02, -0.05])]
+    tg = cuda(random_target(160, 120, seed=7, n_views=3))
+    out = []
+    for timed in (False, True):
+        gm = new_map(p.shape[1], views=3, deterministic=1)
+        gm.set_params(cuda(p))
+        if timed:
+            gm.timing(True)
+        loss = torch.empty(3, device="cuda")
+        for _ in range(3):
+            gm.iterate(cams, tg, loss)
+        torch.cuda.synchronize()
+        if timed:
+            rec = gm.timing_read()
+            for name in ("project", "bin", "raster_fused", "loss", "project_bwd", "adam"):
+                assert rec[name][1] >= 3 and rec[name][0] > 0.0, (name, rec[name])
+        out.append((gm.params().cpu().numpy(), loss.cpu().numpy()))
+        gm.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
