@@ -521,6 +521,7 @@ def run_ours(args):
     roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
     roof["kernel"] = dom
     layout = {"tile": gm.tile_size, "pixels_per_thread": gm.pixels_per_thread}
+    split = split_measure(gm, cam, tgt)
     gm.close()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -543,7 +544,8 @@ def run_ours(args):
             "clocks": clk.summary(),
             "phases_ms": {k: round(v, 5) for k, v in per_all.items()},
             "phases_note": "per-phase device ms from the warm-up graph replays with every phase timed",
-            "work": work, "final_loss": final_loss}
+            "work": work, "final_loss": final_loss,
+            "forward_backward_split": split}
     if rank == 0 and world == 1 and not args.no_extras:
         line["window"] = window_measure(args, max(args.steps, 20), local)
         line["learned_init"] = learned_init_measure(args, local)
@@ -566,6 +568,43 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def split_measure(gm, cam, tgt, steps: int = 20, warmup: int = 3) -> dict:
+    """The forward and the backward timed apart: the same iteration through the separate calls
+    (gs_render, gs_loss, gs_backward, gs_step), each phase bracketed by device events, median of
+    `steps` iterations. The mapping iteration itself runs forward, loss and adjoint as one fused
+    kernel; this is the split the separate kernels give (after the timed regions: it moves the
+    map by steps + warmup Adam steps)."""
+    import statistics
+    import torch
+    names = ("project", "bin", "raster_fwd", "loss", "raster_bwd", "project_bwd", "adam")
+    for _ in range(warmup):
+        gm.render(cam)
+        gm.loss(tgt)
+        gm.backward()
+        gm.step()
+    per = {k: [] for k in names}
+    for _ in range(steps):
+        gm.timing(True)
+        gm.render(cam)
+        gm.loss(tgt)
+        gm.backward()
+        gm.step()
+        torch.cuda.synchronize()
+        rec = gm.timing_read()
+        for k in names:
+            if rec.get(k, (0.0, 0))[1] > 0:
+                per[k].append(rec[k][0])
+    gm.timing(False)
+    med = {k: statistics.median(v) for k, v in per.items() if v}
+    fwd = med.get("project", 0.0) + med.get("bin", 0.0) + med.get("raster_fwd", 0.0)
+    bwd = med.get("raster_bwd", 0.0) + med.get("project_bwd", 0.0)
+    return {"what": "separate calls gs_render | gs_loss | gs_backward | gs_step, per-phase device time, "
+                    f"median of {steps} iterations (the fused iteration merges forward, loss and adjoint)",
+            "forward_ms": round(fwd, 5), "loss_ms": round(med.get("loss", 0.0), 5),
+            "backward_ms": round(bwd, 5), "adam_ms": round(med.get("adam", 0.0), 5),
+            "phases_ms": {k: round(v, 5) for k, v in med.items()}}
 
 
 def window_measure(args, steps: int, device: int = 0) -> dict:
