@@ -278,6 +278,18 @@ int side_begin(gs_ctx* c, cudaStream_t s) {
     return GS_OK;
 }
 
+// An iteration that stopped part-way after side_begin (an error, or the report of a non-finite
+// value): the side stream's zeroing is joined to s, and the other entry points zero on their own
+// stream again. Returns `code`.
+int side_abort(gs_ctx* c, cudaStream_t s, int code) {
+    if (c->side_zeroed) {
+        cudaEventRecord(c->side_ev[4], c->side);
+        cudaStreamWaitEvent(s, c->side_ev[4], 0);
+        c->side_zeroed = false;
+    }
+    return code;
+}
+
 // Projection, depth sort, scan. Leaves P in dcount[0].
 int front_half(gs_ctx* c, const DevConst& k, cudaStream_t s) {
     const uint32_t items = (uint32_t)c->n_views * (uint32_t)c->n;
@@ -866,12 +878,13 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
     ++c->launches;
     k_set_cams<<<1, 32, 0, s>>>(b, c->dcam, c->target_slot);
     CK(cudaGetLastError());
-    if ((code = side_begin(c, s)) != GS_OK) return code;
-    if ((code = front_half(c, k, s)) != GS_OK) return code;
-    CK(cudaMemcpyAsync(c->hcount, c->dcount, sizeof(uint32_t) * 11, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if ((code = check_nonfinite(c, c->hcount[10], s)) != GS_OK) return code;
-    {
+    auto direct = [&]() -> int {
+        int cd;
+        if ((cd = side_begin(c, s)) != GS_OK) return cd;
+        if ((cd = front_half(c, k, s)) != GS_OK) return cd;
+        CK(cudaMemcpyAsync(c->hcount, c->dcount, sizeof(uint32_t) * 11, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if ((cd = check_nonfinite(c, c->hcount[10], s)) != GS_OK) return cd;
         const int64_t P = c->hcount[0];
         c->visible_hint = c->hcount[8];
         c->pairs_hint = (uint32_t)std::min<int64_t>(P, 0xFFFFFFFFll);
@@ -880,10 +893,10 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
         if (P > kMaxPairs) return fail(c, GS_ERR_CAPACITY, "pair count exceeds 2^32");
         if (want > c->pair_cap && alloc_pairs(c, want) != cudaSuccess)
             return fail(c, GS_ERR_OOM, "growing the pair buffers failed");
-    }
-    code = iteration_tail(c, k, target, c->target_slot, rgb, loss_out, false, s);
-    c->side_zeroed = false;   // (also after an error part-way)
-    if (code != GS_OK) return code;
+        return iteration_tail(c, k, target, c->target_slot, rgb, loss_out, false, s);
+    };
+    code = direct();
+    if (code != GS_OK) return side_abort(c, s, code);
     c->adam_t += 1;
     c->rendered_rgb = rgb;
     const int64_t launches0 = c->launches;
@@ -910,6 +923,7 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
         if (cc == GS_OK) cc = front_half(c, k, cs);
         if (cc == GS_OK) cc = iteration_tail(c, k, target, c->target_slot, rgb, loss_out, true, cs);
     }
+    if (cc != GS_OK) side_abort(c, cs, cc);   // joined, so that the capture ends cleanly
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(cs, &g);
     c->capturing = false;

@@ -73,3 +73,35 @@ def test_nonfinite_gradient_leaves_the_parameter_unchanged():
     assert e.value.code == GS_ERR_NONFINITE
     gm.render(cam)   # reported once
     gm.close()
+
+
+@pytest.mark.parametrize("tile,ppt", [(16, 1), (16, 2)])
+def test_report_from_a_first_iteration_leaves_the_map_usable(tile, ppt):
+    """The flag of a non-finite gradient is reported by the first (direct) gs_iterate of a shape,
+    which then stops after the projection: the zeroing it had issued on its second stream must not
+    be taken for done by the calls that follow. Renders after it equal a fresh map's render of the
+    same parameters bit for bit (their work queues start from zero every time), and the mapping
+    iteration then runs."""
+    p, cam = frustum_scene()
+    tg = cuda(random_target(160, 120, seed=3))
+    gm = new_map(p.shape[1], tile_size=tile, pixels_per_thread=ppt)
+    gm.set_params(cuda(p))
+    gm.render(cam)
+    gm.loss(tg)
+    gm.backward()
+    g = gm.grads()
+    g[11, 5] = float("nan")
+    gm.set_grads(g)
+    gm.step()
+    loss = torch.empty(3, device="cuda")
+    assert _iterate(gm, cam, tg, loss) == GS_ERR_NONFINITE
+    ref_map = new_map(p.shape[1], tile_size=tile, pixels_per_thread=ppt)
+    ref_map.set_params(gm.params())
+    ref = ref_map.render(cam).clone()
+    for _ in range(3):
+        assert torch.equal(gm.render(cam), ref)
+    codes = [_iterate(gm, cam, tg, loss) for _ in range(3)]
+    assert codes == [0, 0, 0], codes
+    assert torch.isfinite(loss).all() and torch.isfinite(gm.params()).all()
+    ref_map.close()
+    gm.close()
