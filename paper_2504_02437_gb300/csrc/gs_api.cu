@@ -580,7 +580,10 @@ int gs_render(gs_ctx* c, const gs_camera* cams, int n_views, float* rgb, float* 
     const DevConst k = dev_const(c->cfg);
     c->rendered_rgb = rgb;
     if (c->n == 0) return render_empty(c, rgb, T, argmax, s);
-    if ((code = front_half(c, k, s)) != GS_OK) return code;
+    if ((code = front_half(c, k, s)) != GS_OK) {
+        c->n_views = 0;   // no image to take a loss of
+        return code;
+    }
     // size the pair buffers: read P back (the one synchronisation of a render)
     CK(cudaMemcpyAsync(c->hcount, c->dcount, sizeof(uint32_t) * 11, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -602,7 +605,10 @@ int gs_render(gs_ctx* c, const gs_camera* cams, int n_views, float* rgb, float* 
             return fail(c, GS_ERR_CAPACITY, "pair count exceeds 2^32");
         }
     }
-    if ((code = back_half(c, k, rgb, argmax, s)) != GS_OK) return code;
+    if ((code = back_half(c, k, rgb, argmax, s)) != GS_OK) {
+        c->n_views = 0;
+        return code;
+    }
     CK(launch_copy_T(c, T, s));
     return GS_OK;
 }
@@ -651,9 +657,9 @@ int gs_step(gs_ctx* c, void* stream) {
     if (!c) return GS_ERR_ARG;
     if (!c->backward_ready) return fail(c, GS_ERR_STATE, "gs_step before gs_backward");
     cudaStream_t s = (cudaStream_t)stream;
-    c->adam_t += 1;
     Phase ph(c, GS_PHASE_ADAM, s);
     CK(launch_adam(c, s));
+    c->adam_t += 1;
     c->backward_ready = false;
     return GS_OK;
 }
