@@ -66,24 +66,6 @@ def _ncu_traffic(kernel: str, tile: int, ppt: int):
     return t["bytes"] if h == t["sha256"] else None
 
 
-def _h2d_async():
-    """cudaMemcpyAsync host -> device on a given stream (torch's non_blocking copy_ from pinned
-    memory held the host for the whole copy when the copy stream had pending waits)."""
-    import ctypes
-    rt = ctypes.CDLL("libcudart.so")
-    rt.cudaMemcpyAsync.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p]
-
-    def copy(dst, src, stream):
-        # a raw byte copy: both sides must be contiguous in the same element order
-        assert src.is_pinned() and dst.is_cuda and dst.numel() == src.numel() and dst.dtype == src.dtype
-        assert src.is_contiguous() and dst.is_contiguous()
-        err = rt.cudaMemcpyAsync(dst.data_ptr(), src.data_ptr(), src.numel() * src.element_size(), 1,
-                                 stream.cuda_stream)
-        if err != 0:
-            raise RuntimeError(f"cudaMemcpyAsync failed ({err})")
-    return copy
-
-
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -449,33 +431,19 @@ def run_ours(args):
     value = replica_throughput(args.steps, world, total_ms)
     final_loss = loss.cpu().numpy().tolist()
 
-    # ---- end to end through the API: each step's target goes up from pinned host memory and its
-    # loss comes back. The upload of step k + 1 (copy stream, second target buffer) runs while
-    # step k iterates; step 0's upload sits inside its own bracket. Each step is bracketed on the
-    # compute stream like the device-resident steps, L2 flushed between steps, outside the brackets.
+    # ---- end to end through the API: gs_iterate_host takes the step's target in pinned host memory
+    # and returns its loss there. The library uploads step k's target once step k - 1's iteration
+    # has started (inside that step's bracket, beside its iteration; step 0's inside its own) and
+    # copies the loss back after the iteration. Each step is bracketed on the compute stream like
+    # the device-resident steps, L2 flushed between steps, outside the brackets.
     gm.timing(False)
     tgt_host = torch.as_tensor(np.ascontiguousarray(target[None])).pin_memory()
     loss_host = torch.empty(3).pin_memory()
-    bufs = [torch.empty_like(tgt), torch.empty_like(tgt)]
-    copy_stream = torch.cuda.Stream(device=dev)
-    ready = [torch.cuda.Event() for _ in range(2)]
-    free = [torch.cuda.Event() for _ in range(2)]
-    for bb in bufs:
-        bb.copy_(tgt)
     for _ in range(2):
-        gm.iterate(cam, bufs[0], loss)
+        gm.iterate_host(cam, tgt_host, loss_host)   # records the iteration with the host-loss slot
     torch.cuda.synchronize()
-
-    h2d = _h2d_async()
-
-    def upload(k):
-        copy_stream.wait_event(free[k % 2])
-        h2d(bufs[k % 2], tgt_host, copy_stream)
-        ready[k % 2].record(copy_stream)
     e2e_region_ms = []
     for r in range(R):
-        for e in free:
-            e.record(stream)
         e_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         e_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         barrier(world)
@@ -483,15 +451,7 @@ def run_ours(args):
         for k in range(args.steps):
             flush.zero_()
             e_s[k].record(stream)
-            if k == 0:
-                copy_stream.wait_event(e_s[0])
-                upload(0)
-            if k + 1 < args.steps:
-                upload(k + 1)
-            stream.wait_event(ready[k % 2])
-            gm.iterate(cam, bufs[k % 2], loss)
-            free[k % 2].record(stream)
-            loss_host.copy_(loss, non_blocking=True)
+            gm.iterate_host(cam, tgt_host, loss_host)
             e_e[k].record(stream)
         torch.cuda.synchronize()
         barrier(world)
@@ -536,9 +496,10 @@ def run_ours(args):
             "layout": layout,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(tgt.numel() * 4),
                     "d2h_bytes_per_step": 12,
-                    "how": "target uploaded from pinned host memory on a copy stream (step k+1's during step k), "
-                           "loss read back to pinned memory, each step bracketed, L2 flushed between steps; "
-                           f"median of {R} regions"},
+                    "how": "gs_iterate_host: each step's target uploaded from pinned host memory by the library "
+                           "(on its copy stream, once the previous step's iteration has started: inside that "
+                           "step's bracket), the loss copied back to pinned memory; each step bracketed, L2 "
+                           f"flushed between steps; median of {R} regions"},
             "gpu_launches": int(launches),
             "roofline": roof,
             "clocks": clk.summary(),

@@ -205,6 +205,27 @@ GS_API int gs_step(gs_ctx* ctx, void* stream);
 GS_API int gs_iterate(gs_ctx* ctx, const gs_camera* cams_host, int n_views, const float* target_dev,
                float* loss_dev, float* rgb_dev, void* stream);
 
+/* gs_iterate with the target image and the loss in host memory (the same
+ * mapping iteration, Section 3.2 "Map Optimization", Eq. 3, 10-11).
+ * target_host [n_views][3][H][W] float32 is copied into one of two device
+ * buffers the context owns, on a copy stream of its own: the copy starts once
+ * the previous gs_iterate_host call's iteration has started on its stream (so
+ * with the host ahead of the device it runs beside that iteration) and the
+ * call before that, the last reader of the buffer, is done; this call's
+ * iteration waits for it on `stream`. loss_host (optional, float[3]: total,
+ * photometric, planar) receives the loss by a copy on `stream` after the
+ * iteration: it holds the values once the stream has reached that point
+ * (synchronise the stream or an event recorded after the call). Pinned host
+ * memory (cudaMallocHost or equivalent) keeps both copies asynchronous;
+ * pageable memory works, with the host then waiting for the copies. The
+ * caller must not change target_host before the stream has passed the call.
+ * rgb_dev as in gs_iterate. Errors as gs_iterate, plus GS_ERR_ARG for a NULL
+ * target_host or an invalid camera and GS_ERR_OOM when the target buffers
+ * cannot grow. gs_iterate with loss_dev NULL and gs_iterate_host write the
+ * loss to one internal slot, so alternating the two keeps one recorded graph. */
+GS_API int gs_iterate_host(gs_ctx* ctx, const gs_camera* cams_host, int n_views, const float* target_host,
+                           float* loss_host, float* rgb_dev, void* stream);
+
 /* Dynamic insertion for keyframe `cam` (Eq. 7 reading, Section 3.2 "Dynamic
  * 3D Gaussian Insertion"): renders the accumulated opacity of the current map
  * in that view; a point of points_dev ([n][3] world xyz) that projects in

@@ -62,6 +62,7 @@ SIGNATURES = {
     "gs_backward": (_I, [_P, _P, _P]),
     "gs_step": (_I, [_P, _P]),
     "gs_iterate": (_I, [_P, C.POINTER(gs_camera), _I, _P, _P, _P, _P]),
+    "gs_iterate_host": (_I, [_P, C.POINTER(gs_camera), _I, _P, _P, _P, _P]),
     "gs_count_dominant": (_I, [_P, C.POINTER(gs_camera), _I, _P]),
     "gs_timing_phases": (_I, [_P, C.c_uint32]),
     "gs_insert": (_I, [_P, C.POINTER(gs_camera), _P, _P, _I, C.POINTER(_I), _P, _P]),

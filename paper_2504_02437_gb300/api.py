@@ -28,12 +28,25 @@ def _ptr(t: Optional[torch.Tensor]) -> Optional[C.c_void_p]:
     return C.c_void_p(t.data_ptr())
 
 
-def _f32(t: Optional[torch.Tensor], shape: tuple, name: str) -> Optional[torch.Tensor]:
-    """A float32 CUDA tensor of the given shape, passed without a copy (None stays None)."""
+def _hptr(t: Optional[torch.Tensor]) -> Optional[C.c_void_p]:
+    if t is None:
+        return None
+    if t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous host tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _f32(t: Optional[torch.Tensor], shape: tuple, name: str, host: bool = False) -> Optional[torch.Tensor]:
+    """A contiguous float32 tensor of the given shape, on the GPU (host=False) or in host memory,
+    passed without a copy (None stays None)."""
     if t is None:
         return None
     if t.dtype != torch.float32 or tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name}: expected float32 {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous tensor")
+    if t.is_cuda == host:
+        raise ValueError(f"{name}: expected a {'host' if host else 'CUDA'} tensor")
     return t
 
 
@@ -189,6 +202,27 @@ class GaussianMap:
         _f32(rgb_out, (V, 3, H, W), "rgb_out")
         self._check(self.lib.gs_iterate(self.ctx, arr, V, _ptr(target), _ptr(loss_out), _ptr(rgb_out), _stream()))
         self._last_views, self._last_hw = V, (H, W)
+        return loss_out
+
+    def iterate_host(self, cams, target: torch.Tensor, loss_out: Optional[torch.Tensor] = None,
+                     rgb_out: Optional[torch.Tensor] = None) -> Optional[torch.Tensor]:
+        """The mapping iteration with the target [V, 3, H, W] and the loss [3] in host memory
+        (pinned keeps the copies asynchronous): the library uploads the target while the
+        projection and the sorts run and copies the loss back on the current stream (read it after
+        synchronising). The target must stay unchanged until the stream has passed the call."""
+        arr, V, H, W = _cams(cams)
+        _f32(target, (V, 3, H, W), "target", host=True)
+        _f32(loss_out, (3,), "loss_out", host=True)
+        _f32(rgb_out, (V, 3, H, W), "rgb_out")
+        self._check(self.lib.gs_iterate_host(self.ctx, arr, V, _hptr(target), _hptr(loss_out), _ptr(rgb_out),
+                                             _stream()))
+        self._last_views, self._last_hw = V, (H, W)
+        # the host buffers stay referenced until the stream has passed the call (the upload and the
+        # loss copy have run): a pinned block torch frees can be handed out again at once
+        done = torch.cuda.Event()
+        done.record()
+        self._host_inflight = [x for x in getattr(self, "_host_inflight", []) if not x[0].query()]
+        self._host_inflight.append((done, target, loss_out))
         return loss_out
 
     # ---- map management

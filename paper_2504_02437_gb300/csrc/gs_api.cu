@@ -453,6 +453,10 @@ int gs_create(const gs_config* cfg, int device, gs_ctx** out) {
         for (int i = 0; i < 6; ++i)
             ok = ok && cudaEventCreateWithFlags(&c->side_ev[i], cudaEventDisableTiming) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&c->graph_done, cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking) == cudaSuccess;
+        for (int i = 0; i < 2; ++i)
+            for (cudaEvent_t* ev : {&c->h2d_start[i], &c->h2d_ready[i], &c->h2d_free[i]})
+                ok = ok && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) == cudaSuccess;
         if (!ok) { code = fail(c, GS_ERR_OOM, "device allocation failed"); break; }
         uint32_t init[16] = {0, 0, 0, 0xFFFFFFFFu, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         e = cudaMemcpy(c->dcount, init, sizeof(init), cudaMemcpyHostToDevice);
@@ -489,7 +493,7 @@ void gs_destroy(gs_ctx* c) {
                     c->tiles_touched, c->depth, c->dkey[0], c->dkey[1], c->dval[0], c->dval[1], c->offsets, c->ranges,
                     c->work_order, c->work_order_next, c->work_order_graph, c->T_final, c->n_last, c->dLdC, c->grad2d, c->hist, c->vis_blocks, (void*)c->target_slot, c->ssim_maps, c->ssim_part, c->dcount,
                     c->partials, c->psnr_part, c->reg_part, c->tile_part, c->fpart,
-                    c->own_rgb};
+                    c->own_rgb, c->tgt_stage[0], c->tgt_stage[1]};
     for (void* p : ptrs) cudaFree(p);
     free_pairs(c);
     if (c->hcount) cudaFreeHost(c->hcount);
@@ -499,6 +503,10 @@ void gs_destroy(gs_ctx* c) {
     for (int i = 0; i < 6; ++i)
         if (c->side_ev[i]) cudaEventDestroy(c->side_ev[i]);
     if (c->graph_done) cudaEventDestroy(c->graph_done);
+    if (c->copy) cudaStreamDestroy(c->copy);
+    for (int i = 0; i < 2; ++i)
+        for (cudaEvent_t ev : {c->h2d_start[i], c->h2d_ready[i], c->h2d_free[i]})
+            if (ev) cudaEventDestroy(ev);
     delete c;
 }
 
@@ -788,12 +796,10 @@ static int autotune(gs_ctx* c, const gs_camera* cams, int n_views, const float* 
     return GS_OK;
 }
 
-int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* target, float* loss_dev, float* rgb,
-               void* stream) {
-    if (!c) return GS_ERR_ARG;
-    if (!target) return fail(c, GS_ERR_ARG, "target_dev is NULL");
+// The mapping iteration (gs_iterate without the argument checks).
+static int iterate_core(gs_ctx* c, const gs_camera* cams, int n_views, const float* target, float* loss_dev,
+                        float* rgb, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
-    CK(cudaSetDevice(c->device));
     if (n_views < 1 || n_views > c->cfg.max_views || !cams) return fail(c, GS_ERR_ARG, "bad views");
     if (!rgb) {
         size_t need = (size_t)n_views * 3 * cams[0].width * cams[0].height;
@@ -985,6 +991,55 @@ int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* targe
     c->graph_loss = loss_out;
     c->graph_rgb = rgb;
     c->graph_timing = c->timing;
+    return GS_OK;
+}
+
+int gs_iterate(gs_ctx* c, const gs_camera* cams, int n_views, const float* target, float* loss_dev, float* rgb,
+               void* stream) {
+    if (!c) return GS_ERR_ARG;
+    if (!target) return fail(c, GS_ERR_ARG, "target_dev is NULL");
+    CK(cudaSetDevice(c->device));
+    return iterate_core(c, cams, n_views, target, loss_dev, rgb, stream);
+}
+
+int gs_iterate_host(gs_ctx* c, const gs_camera* cams, int n_views, const float* target_host, float* loss_host,
+                    float* rgb, void* stream) {
+    if (!c) return GS_ERR_ARG;
+    if (!target_host) return fail(c, GS_ERR_ARG, "target_host is NULL");
+    if (n_views < 1 || n_views > c->cfg.max_views || !cams) return fail(c, GS_ERR_ARG, "bad views");
+    if (!camera_ok(cams[0], c->cfg)) return fail(c, GS_ERR_ARG, "invalid camera");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(c->device));
+    const size_t elems = (size_t)n_views * 3 * cams[0].width * cams[0].height;
+    if (elems > c->tgt_stage_elems) {
+        CK(cudaStreamSynchronize(c->copy));
+        for (int i = 0; i < 2; ++i) CK(cudaEventSynchronize(c->h2d_free[i]));   // the buffers' last readers
+        for (int i = 0; i < 2; ++i) {
+            cudaFree(c->tgt_stage[i]);
+            c->tgt_stage[i] = nullptr;
+        }
+        c->tgt_stage_elems = 0;
+        for (int i = 0; i < 2; ++i)
+            if (dalloc(&c->tgt_stage[i], elems) != cudaSuccess) return fail(c, GS_ERR_OOM, "target buffers");
+        c->tgt_stage_elems = elems;
+    }
+    // the upload starts once the previous call's iteration has started on its stream (with the
+    // host ahead of the device it runs beside that iteration) and the one before, the last reader
+    // of this buffer, is done; this call's iteration waits for it. Host-side stream waits only:
+    // each resolves to the record made by the call named, so no wait can refer to later work.
+    const int k = c->h2d_k;
+    CK(cudaStreamWaitEvent(c->copy, c->h2d_start[k ^ 1], 0));
+    CK(cudaStreamWaitEvent(c->copy, c->h2d_free[k], 0));
+    CK(cudaMemcpyAsync(c->tgt_stage[k], target_host, sizeof(float) * elems, cudaMemcpyHostToDevice, c->copy));
+    CK(cudaEventRecord(c->h2d_ready[k], c->copy));
+    CK(cudaEventRecord(c->h2d_start[k], s));
+    CK(cudaStreamWaitEvent(s, c->h2d_ready[k], 0));
+    c->h2d_k = k ^ 1;
+    const int code = iterate_core(c, cams, n_views, c->tgt_stage[k], nullptr, rgb, stream);
+    CK(cudaEventRecord(c->h2d_free[k], s));
+    if (code != GS_OK) return code;
+    if (loss_host)
+        CK(cudaMemcpyAsync(loss_host, c->partials + c->n_partials, sizeof(float) * 3, cudaMemcpyDeviceToHost, s));
     return GS_OK;
 }
 

@@ -179,6 +179,16 @@ struct gs_ctx {
     std::vector<TimedNode> graph_tnodes;    // event-record nodes around each phase
     float* own_rgb = nullptr;               // internal image when the caller gives none
     size_t own_rgb_elems = 0;
+    // gs_iterate_host: the caller's host targets go up, alternately into two device buffers, on
+    // `copy`; call k's upload waits for the start of call k-1's iteration on the caller's stream
+    // (h2d_start) and the end of call k-2's (h2d_free, the last reader of its buffer), and call k's
+    // iteration waits for it (h2d_ready): host-side stream waits only, so with the host ahead of the
+    // device an upload runs beside the previous iteration
+    cudaStream_t copy = nullptr;
+    cudaEvent_t h2d_start[2] = {}, h2d_ready[2] = {}, h2d_free[2] = {};
+    float* tgt_stage[2] = {};
+    size_t tgt_stage_elems = 0;
+    int h2d_k = 0;                          // buffer of the next call
     // phase timing (gs_timing_enable / gs_timing_read)
     uint32_t timing = 0;                 // bit p: phase p is timed
     struct TimingRec {
