@@ -393,7 +393,8 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
                                          const uint32_t* __restrict__ emit_item, const float4* __restrict__ rec,
                                          const DevConst& kc, float (&T)[PPT], const uint32_t (&cnt_last)[PPT],
                                          const float (&gr)[PPT], const float (&gg)[PPT], const float (&gb)[PPT],
-                                         float* __restrict__ grad2d, float* __restrict__ pairgrad, int staged) {
+                                         float* __restrict__ grad2d, float* __restrict__ pairgrad, int staged,
+                                         bool fwd_masks) {
     constexpr int NT = Layout<TILE, PPT>::kThreads;
     constexpr int kBatch = batch_for(NT);
     Stage<kBatch, NT / 32>& st = stage<kBatch, NT / 32>();
@@ -439,6 +440,9 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
             }
             nk = lo;
         } else {
+            // the forward's warp masks of a one-batch tile are still staged (nothing writes them
+            // in between): only the records are staged again
+            const bool keep_masks = fwd_masks && rg.y - rg.x <= (uint32_t)kBatch;
             __syncthreads();
             for (int i = threadIdx.x; i < kBatch; i += NT) {
                 const uint32_t j = bs + i;
@@ -447,7 +451,7 @@ __device__ __forceinline__ void bwd_core(const TileGeom<TILE, PPT>& g, const uin
                     const uint32_t item = DET ? emit_item[pv] : pv;
                     stage_record(rec, item, g.ox, g.oy, kc.alpha_min, s0[i], s1[i], s2[i]);
                     sid[i] = pv;
-                    st.mask[i] = warp_mask<TILE, PPT>(g, s0[i], s1[i], s2[i].w);
+                    if (!keep_masks) st.mask[i] = warp_mask<TILE, PPT>(g, s0[i], s1[i], s2[i].w);
                 }
             }
             __syncthreads();
@@ -621,7 +625,7 @@ __global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads)
                 gb[p] = dLdC[(size_t)g.view * 3 * HW + 2 * HW + pix];
             }
         }
-        bwd_core<TILE, PPT, DET>(g, pval, emit_item, rec, kc, T, cnt, gr, gg, gb, grad2d, pairgrad, -1);
+        bwd_core<TILE, PPT, DET>(g, pval, emit_item, rec, kc, T, cnt, gr, gg, gb, grad2d, pairgrad, -1, false);
     }
 }
 
@@ -685,7 +689,7 @@ __global__ void __launch_bounds__(Layout<TILE, PPT>::kThreads, Layout<TILE, PPT>
             __syncthreads();
         }
         bwd_core<TILE, PPT, DET>(g, pval, emit_item, rec, kc, T, last, gr, gg, gb, grad2d, pairgrad,
-                                 (DET || !Layout<TILE, PPT>::kReuseStaged) ? -1 : staged);
+                                 (DET || !Layout<TILE, PPT>::kReuseStaged) ? -1 : staged, true);
     }
     // per-CTA photometric partial (already scaled)
     __shared__ float red[32];
