@@ -781,3 +781,51 @@ def test_gradient_finite_differences_with_ssim(seed, n):
     # the SSIM term changes the gradient (it is not the L1 gradient)
     g1 = O.loss_and_grads(p, [cam], tg)["grad"]
     assert np.abs(g - g1).max() > 1e-3 * np.abs(g1).max()
+
+
+def test_pixel_box_matches_brute_force():
+    """The membership box of a pixel-exact test |px - u| <= r, |py - v| <= r, clipped to the
+    image, against a scan of every pixel (means inside, outside and on integer coordinates)."""
+    rng = np.random.default_rng(11)
+    W, H = 23, 17
+    cases = [(u, v, r) for u, v, r in zip(rng.uniform(-6, W + 6, 300), rng.uniform(-6, H + 6, 300),
+                                          rng.integers(0, 7, 300))]
+    cases += [(4.0, 3.0, 2), (0.0, 0.0, 0), (W - 1.0, H - 1.0, 1), (-2.0, 5.5, 2), (5.5, H + 2.0, 3)]
+    px, py = np.arange(W), np.arange(H)
+    for u, v, r in cases:
+        x0, x1, y0, y1 = O.pixel_box(np.float64(u), np.float64(v), np.float64(r), W, H)
+        xs = px[np.abs(px - u) <= r]
+        ys = py[np.abs(py - v) <= r]
+        if xs.size == 0 or ys.size == 0:
+            assert x0 > x1 or y0 > y1, (u, v, r, x0, x1, y0, y1)
+        else:
+            assert (x0, x1, y0, y1) == (xs[0], xs[-1], ys[0], ys[-1]), (u, v, r)
+
+
+def test_bf16_round_is_round_to_nearest_even():
+    """bfloat16 rounding against an integer restatement on the float32 bit patterns (keep the top
+    16 bits, add half an ulp plus the kept LSB for ties to even), and hand-checked ties."""
+    rng = np.random.default_rng(12)
+    x = np.concatenate([rng.standard_normal(4000) * 10.0 ** rng.integers(-6, 6, 4000),
+                        [0.0, -0.0, 1.0, -3.5, 65504.0, 1e-30]]).astype(np.float32)
+    bits = x.view(np.uint32).astype(np.uint64)
+    rounded = ((bits + 0x7FFF + ((bits >> 16) & 1)) & 0xFFFF0000).astype(np.uint32).view(np.float32)
+    got = O.bf16_round(x).numpy()
+    assert np.array_equal(got, rounded.astype(np.float64))
+    # ties: 1 + 2^-8 is halfway between 1 and 1 + 2^-7 (even: 1); 1 + 3 * 2^-8 between 1 + 2^-7 and
+    # 1 + 2^-6 (even: 1 + 2^-6)
+    ties = O.bf16_round(np.float32([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8])).numpy()
+    assert ties.tolist() == [1.0, 1 + 2.0 ** -6]
+
+
+def test_ssim_window_closed_form():
+    """The 11 x 11 window: w[i, j] = g_i g_j with g_k proportional to exp(-k^2 / (2 1.5^2)), sum 1.
+    Checked by its ratios (no normalisation needed) and its sum."""
+    w = O.ssim_window().numpy()
+    assert w.shape == (11, 11)
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.allclose(w, w.T, rtol=0, atol=0) and np.allclose(w, w[::-1, ::-1], rtol=0, atol=0)
+    assert math.isclose(w[5, 5] / w[0, 0], math.exp((25 + 25) / (2 * 1.5 ** 2)), rel_tol=1e-12)
+    assert math.isclose(w[5, 5] / w[5, 8], math.exp(9 / (2 * 1.5 ** 2)), rel_tol=1e-12)
+    g1 = np.exp(-np.arange(-5, 6) ** 2 / (2 * 1.5 ** 2))
+    assert np.allclose(w, np.outer(g1, g1) / g1.sum() ** 2, rtol=1e-14, atol=0)
