@@ -300,6 +300,25 @@ def test_bin_pairs_brute_force(tile):
     assert cnt.sum() == len(ref)
 
 
+def test_bin_pairs_equal_depths_keep_id_order():
+    """Gaussians at equal depth in one tile are ordered by id (the sort is stable on the
+    depth-sorted item order): depths snapped to three values, against the brute force."""
+    p, cam = frustum_scene(n=60, width=37, height=29, fx=40, fy=40, cx=18.5, cy=14.5, seed=12)
+    pr = O.project(torch.tensor(p, dtype=torch.float64), cam)
+    u = pr["u"].numpy().astype(np.float32).astype(np.float64)
+    v = pr["v"].numpy().astype(np.float32).astype(np.float64)
+    r, ok = pr["r"].numpy(), pr["valid"].numpy()
+    d = np.float32([1.5, 2.0, 2.5])[np.arange(len(u)) % 3]
+    keys, vals = O.bin_pairs(u, v, r, d, ok, cam.width, cam.height, 8)
+    ref = _brute_pairs(u, v, r, d, ok, cam.width, cam.height, 8)
+    assert [(int(k), int(x)) for k, x in zip(keys, vals)] == ref
+    # the case is not vacuous: some tile holds several Gaussians of one depth
+    ties = {}
+    for k, x in ref:
+        ties[k] = ties.get(k, 0) + 1
+    assert max(ties.values()) >= 3
+
+
 # ------------------------------------------------------------------ Eq. 10-11 and gradients
 
 
