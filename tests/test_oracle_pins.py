@@ -214,6 +214,19 @@ def test_transmittance_is_product():
     np.testing.assert_allclose(out["rgb"][0], expect, rtol=1e-12)
 
 
+def test_equal_depths_blend_in_id_order():
+    """Two layers at the same depth (o = 0.6 and 0.3): the lower id blends first, so
+    C = 0.6 c0 + 0.3 (1 - 0.6) c1; swapping the array order swaps which colour is in front."""
+    red, blue = [1, 0, 0], [0, 0, 1]
+    p = _stack([0.6, 0.3], [red, blue], [2.0, 2.0])
+    out = O.render(p, _axis_cam(), pixels=np.array([[32, 32]]))
+    np.testing.assert_allclose(out["rgb"][0], [0.6, 0.0, 0.12], rtol=1e-13, atol=1e-16)
+    p = _stack([0.3, 0.6], [blue, red], [2.0, 2.0])
+    out = O.render(p, _axis_cam(), pixels=np.array([[32, 32]]))
+    np.testing.assert_allclose(out["rgb"][0], [0.42, 0.0, 0.3], rtol=1e-13, atol=1e-16)
+    np.testing.assert_allclose(out["T"][0], 0.28, rtol=1e-13)
+
+
 def test_alpha_min_is_strict_threshold():
     c = [0.5, 0.25, 1.0]
     for o, blends in [(1 / 255 + 1e-6, True), (1 / 255 - 1e-6, False)]:
